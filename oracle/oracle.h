@@ -1,0 +1,95 @@
+/*
+ * oracle.h -- plain, slow CPU reference for Talek's server-side state.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the CUDA library
+ * against the paper.  Only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant with the CUDA library, and it never calls it.
+ *
+ * Naming: n = number of buckets (the paper's b), d = slots per bucket,
+ * z = message bytes per slot.  A bucket is d*z contiguous bytes; the table is
+ * n buckets back to back.  Request vectors are packed LSB-first in 64-bit
+ * words: bit k is bit (k % 64) of word k / 64; bits at positions >= n are
+ * ignored.
+ */
+#ifndef TALEK_ORACLE_H
+#define TALEK_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL (-1)
+#define ORACLE_ENOMEM (-2)
+#define ORACLE_EFULL (-3)
+
+/* ---- IT-PIR (Section 2) ------------------------------------------------ */
+
+/* Server answer, Section 2 step 5: out = XOR of every bucket T[k] whose bit
+ * q[k] is 1.  out has d*z bytes. */
+void oracle_read(const uint8_t *T, uint64_t n, uint32_t d, uint32_t z,
+                 const uint64_t *q, uint8_t *out);
+
+/* B independent answers; R has B rows of ceil(n/64) words, out B rows of d*z. */
+void oracle_read_batch(const uint8_t *T, uint64_t n, uint32_t d, uint32_t z,
+                       const uint64_t *R, uint32_t B, uint8_t *out);
+
+/* Client reconstruction, Section 2 step 6: out = R_1 XOR ... XOR R_l. */
+void oracle_reconstruct(const uint8_t *replies, uint32_t l, uint64_t bytes, uint8_t *out);
+
+/* splitmix64 sequential generator (Steele, Lea & Flood 2014): advances *state
+ * and returns the next output. */
+uint64_t oracle_splitmix64_next(uint64_t *state);
+
+/* ---- blocked cuckoo table with FIFO garbage collection (Section 5.3) --- */
+
+typedef struct oracle_cuckoo oracle_cuckoo;
+
+/* capacity = number of messages kept (0 = never collect); max_evictions =
+ * bound on the eviction walk; seed = s_cuckoo. NULL on bad arguments. */
+oracle_cuckoo *oracle_cuckoo_create(uint64_t n, uint32_t d, uint32_t z, uint64_t capacity,
+                                    uint32_t max_evictions, uint64_t seed);
+void oracle_cuckoo_destroy(oracle_cuckoo *c);
+
+/* Insert one message with candidate buckets b1, b2.  Returns ORACLE_OK,
+ * ORACLE_EINVAL (bucket out of range) or ORACLE_EFULL (eviction bound hit:
+ * table, metadata and the collected item are restored; the random draws made
+ * stay consumed).  *evictions = number of evictions made. */
+int oracle_cuckoo_insert(oracle_cuckoo *c, uint64_t b1, uint64_t b2, const uint8_t *msg,
+                         uint32_t *evictions);
+
+const uint8_t *oracle_cuckoo_table(const oracle_cuckoo *c);
+uint64_t oracle_cuckoo_live(const oracle_cuckoo *c);
+/* Slot metadata; returns 1 if the slot holds an item (and fills b1, b2, seq). */
+int oracle_cuckoo_slot(const oracle_cuckoo *c, uint64_t slot, uint64_t *b1, uint64_t *b2,
+                       uint64_t *seq);
+
+/* ---- Bloom interest vectors (Section 7) -------------------------------- */
+
+typedef struct oracle_bloom oracle_bloom;
+
+/* m bits, k positions per insert, a window of the `window` most recent deltas;
+ * each delta summarises `writes_per_delta` writes (0 = a single delta that is
+ * never replaced).  A new delta opens, in place of the oldest, at the first
+ * write that finds the current one complete. */
+oracle_bloom *oracle_bloom_create(uint64_t m, uint32_t k, uint32_t window,
+                                  uint32_t writes_per_delta);
+void oracle_bloom_destroy(oracle_bloom *b);
+/* Set k positions (each < m) in the current delta. Returns ORACLE_EINVAL on a
+ * position out of range (nothing changes). */
+int oracle_bloom_insert(oracle_bloom *b, const uint64_t *positions);
+/* OR a whole m-bit interest vector (ceil(m/64) words) into the current delta;
+ * counts as one write. Bits >= m are ignored. */
+void oracle_bloom_or_vector(oracle_bloom *b, const uint64_t *vec);
+/* Global interest vector = OR of the deltas in the window (ceil(m/64) words). */
+void oracle_bloom_get(const oracle_bloom *b, uint64_t *out_words);
+/* 1 if all k positions are set in the global interest vector. */
+int oracle_bloom_contains(const oracle_bloom *b, const uint64_t *positions);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
