@@ -1,0 +1,404 @@
+"""Benchmark of the Talek server read path on GB300 (one JSON line on rank 0).
+
+Workload (paper scale): a blocked cuckoo table of n = 32768 buckets x d = 4
+slots x 1024-byte messages (128 MiB, uniform random bytes, seed 0); one step
+serves 32000 simulated users issuing one PIR read each (Bernoulli(0.5)
+request vectors), in batches of B = 256 requests per table pass.  Four copies
+of the table (512 MiB in all, more than the 126 MB L2) are read in rotation,
+so every pass streams its table from HBM.
+
+Reported: reads/s of the step (`value`), per-batch-width legs (B = 1 plain
+kernel, 32, 256) with their table-scan GB/s, the end-to-end rate through the
+synchronous host-buffer entry point (`e2e`), the oracle timed on the host
+(`cpu_baseline`), a short continuous-batching serve run (p50/p99), SM clocks
+sampled during the timed region, and the roofline of the dominant kernel.
+
+Multi-GPU: every rank serves its own 32000 reads from its own replica of the
+table (the paper's servers each hold a full copy); no data-path collective,
+weak scaling.  `--impl reference` times the CPU oracle instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_BUCKETS, D_SLOTS, MSG_BYTES = 32768, 4, 1024
+USERS = 32000
+B_HEAD = 256
+COPIES = 4
+HBM_PEAK_FALLBACK = 6800.0
+SMS, LOP3_PER_CLK_PER_SM = 152, 64
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return {}
+
+
+def alu_peak_tops(sm_mhz: float) -> float:
+    """LOP3 (32-bit conditional-XOR word op) peak: SMs x lanes/clk x clock."""
+    return SMS * LOP3_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args) -> None:
+    """The oracle, as it stands, on the host cores: a bounded sample of the
+    same workload (reads of the 128 MiB table) per step."""
+    import oracle
+    from paper_2001_08250_gb300 import synth
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    T = synth.table_bytes(N_BUCKETS, D_SLOTS, MSG_BYTES, seed=0)
+    R = synth.random_bits(USERS, N_BUCKETS, seed=1)
+    per_step = 4
+    for s in range(args.warmup):
+        oracle.read_batch(T, N_BUCKETS, D_SLOTS, MSG_BYTES, R[s * per_step:(s + 1) * per_step])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        i = (args.warmup + s) * per_step % USERS
+        oracle.read_batch(T, N_BUCKETS, D_SLOTS, MSG_BYTES, R[i:i + per_step])
+    dt = time.perf_counter() - t0
+    v = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "pir_reads_per_s", "value": v, "unit": "reads/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": v, "unit": "reads/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} reads of the 128 MiB table per step"},
+        "e2e": {"value": v, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args) -> dict:
+    return {"workload": "paper-scale PIR reads: n=32768 buckets, d=4, 1024-byte messages "
+                        "(128 MiB table), 32000 Bernoulli(0.5) reads per step, batch width 256",
+            "n": N_BUCKETS, "d": D_SLOTS, "msg_bytes": MSG_BYTES, "reads_per_step": USERS,
+            "batch": B_HEAD, "parallelism": f"replicas x{args.gpus}",
+            "l2": f"{COPIES} rotated table copies ({COPIES * 128} MiB) > L2 per pass"}
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2001_08250_gb300 import build, synth, talekpir
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    L = talekpir.lib()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.Stream()
+    n, d, z = N_BUCKETS, D_SLOTS, MSG_BYTES
+    row = d * z
+    T = synth.table_bytes(n, d, z, seed=0)
+    dbs = []
+    for _ in range(COPIES):
+        db = talekpir.DB(n, d, z)
+        db.load(T)
+        dbs.append(db)
+    R = synth.random_bits(USERS, n, seed=1 + rank)
+    dR = torch.from_numpy(R.view(np.int64)).cuda()
+    dO = torch.empty((USERS, row), dtype=torch.uint8, device="cuda")
+    words = R.shape[1]
+
+    def run_step(B, events=None):
+        for i, b0 in enumerate(range(0, USERS, B)):
+            nb = min(B, USERS - b0)
+            if events is not None:
+                events[i][0].record(stream)
+            dbs[i % COPIES].read_batch_async(dR[b0:b0 + nb], nb, dO[b0:b0 + nb], stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    def timed(B, steps, warmup, with_launch_events=False, clocks=None):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                run_step(B)
+        torch.cuda.synchronize()
+        nb = (USERS + B - 1) // B
+        ev = None
+        per_launch = []
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(steps):
+            if with_launch_events:
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(nb)]
+            run_step(B, ev)
+            if with_launch_events:
+                per_launch.append(ev)
+        end.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        barrier()
+        ms = start.elapsed_time(end) / steps
+        durs = [a.elapsed_time(b) for evs in per_launch for a, b in evs]
+        return ms, durs, ck
+
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
+    table_bytes = n * row
+    algo_bytes_per_read = table_bytes + n / 8 + row  # table + request bits + reply
+
+    # ---- headline: batch width 256, batched kernel
+    clocks = ClockSampler(local)
+    ms, durs, ck = timed(B_HEAD, args.steps, args.warmup, with_launch_events=True, clocks=clocks)
+    ms = max_over_ranks(ms)
+    value = USERS * world / (ms * 1e-3)
+    launch_ms = statistics.mean(durs)
+    ops_per_launch = B_HEAD * n * (row // 4)
+    sm_mhz = (ck or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    achieved_tops = ops_per_launch / (launch_ms * 1e-3) / 1e12
+    peak_tops = alu_peak_tops(sm_mhz)
+
+    # ---- legs: plain (B=1) and B=32
+    legs = {}
+    for B, steps in ((1, max(2, args.steps // 4)), (32, max(3, args.steps // 2))):
+        bms, bd, _ = timed(B, steps, 1, with_launch_events=(B == 1))
+        bms = max_over_ranks(bms)
+        legs[str(B)] = {"reads_per_s": USERS * world / (bms * 1e-3), "ms_per_step": bms}
+        if B == 1:
+            pl_ms = statistics.mean(bd)
+            legs["1"]["scan_gbs"] = algo_bytes_per_read / (pl_ms * 1e-3) / 1e9
+            legs["1"]["launch_ms"] = pl_ms
+        else:
+            legs[str(B)]["scan_gbs"] = (USERS / B) * table_bytes / (bms * 1e-3) / 1e9
+    legs[str(B_HEAD)] = {"reads_per_s": value, "ms_per_step": ms,
+                         "scan_gbs": (USERS / B_HEAD) * table_bytes / (ms * 1e-3) / 1e9,
+                         "launch_ms": launch_ms}
+    plain_gbs = legs["1"]["scan_gbs"]
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    hR = torch.from_numpy(R.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    hO = torch.empty((USERS, row), dtype=torch.uint8).pin_memory().numpy()
+
+    def e2e_step():
+        for i, b0 in enumerate(range(0, USERS, B_HEAD)):
+            nb = min(B_HEAD, USERS - b0)
+            rc = L.tpir_read_batch(dbs[i % COPIES].h, hR[b0:b0 + nb].ctypes.data, nb,
+                                   hO[b0:b0 + nb].ctypes.data)
+            assert rc == 0, rc
+    for _ in range(args.warmup):
+        e2e_step()
+    e2e_steps = max(2, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+    e2e = {"value": USERS * world / e2e_s, "unit": "reads/s",
+           "h2d_bytes_per_step": int(USERS * words * 8), "d2h_bytes_per_step": int(USERS * row)}
+
+    # ---- short serve run (continuous batching), rank 0 only
+    serve = None
+    if not args.no_serve and rank == 0:
+        serve = serve_leg(talekpir, synth, args.serve_rate, args.serve_seconds)
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
+    cpu = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        sample = 8
+        t0 = time.perf_counter()
+        oracle.read_batch(T, n, d, z, R[:sample])
+        cdt = time.perf_counter() - t0
+        cpu = {"value": sample / cdt, "unit": "reads/s", "cores": 1, "kind": "oracle",
+               "sample": f"{sample} reads of the 128 MiB table (single-threaded C)"}
+
+    gpu_launches = args.steps * ((USERS + B_HEAD - 1) // B_HEAD) * 2
+    if rank == 0:
+        line = {
+            "metric": "pir_reads_per_s", "value": value, "unit": "reads/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": workload_config(args),
+            "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": ck,
+            "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
+                         "unit": "Top/s", "frac": achieved_tops / peak_tops, "traffic": None,
+                         "kernel": "batched_scan_kernel (+ zero_outputs_kernel)",
+                         "peak_basis": f"{SMS} SMs x {LOP3_PER_CLK_PER_SM} LOP3/clk x {sm_mhz:.0f} MHz (median SM clock sampled)"},
+            "roofline_plain": {"bound": "hbm", "achieved": plain_gbs, "peak": hbm_peak,
+                               "unit": "GB/s", "frac": plain_gbs / hbm_peak, "traffic": None,
+                               "kernel": "plain_scan_kernel", "peak_basis": "of measured" if peaks else "of fallback"},
+            "legs": legs,
+            "speedup_batched_vs_plain": value / legs["1"]["reads_per_s"],
+            "serve": serve,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    for db in dbs:
+        db.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def serve_leg(talekpir, synth, rate: float, seconds: float) -> dict:
+    """Open-loop Poisson arrivals (10% writes with k = 4 Bloom positions) over
+    eight resident tables of 2^15..2^18 buckets x 4 x 1 KiB; latency is
+    measured from each op's scheduled arrival time."""
+    import threading
+    srv = talekpir.Server(hbm_budget_bytes=64 << 30, max_batch=256, max_inflight=2)
+    sizes = [1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 15, 1 << 16, 1 << 17, 1 << 15]
+    tids = []
+    for s in sizes:
+        tid = srv.add_table(s, 4, 1024)
+        db = srv.table(tid)
+        db.bloom_create(1 << 20, 4, window=4, writes_per_delta=1000)
+        tids.append(tid)
+    count = int(rate * seconds)
+    arr = synth.poisson_arrivals(rate, count, seed=5)
+    is_w = synth.op_mix(count, 0.1, seed=5)
+    tsel = (synth.stream(synth.stream_key(5, 99), count) % np.uint64(len(tids))).astype(np.int64)
+    keys = synth.write_keys(count, seed=6)
+    reqs = {t: synth.random_bits(64, sizes[t], seed=7, table=t) for t in tids}
+    msg = synth.messages(64, 1024, seed=8)
+    outs = np.empty((count, 4096), dtype=np.uint8)
+    done = [0]
+
+    def poller():
+        while done[0] < count:
+            done[0] += len(srv.poll())
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.monotonic_ns()
+    for i in range(count):
+        ta = t0 + int(arr[i] * 1e9)
+        while time.monotonic_ns() < ta:
+            pass
+        t = int(tsel[i])
+        if is_w[i]:
+            b1, b2 = synth.bucket_pairs(keys[i:i + 1], sizes[t])
+            pos = synth.bloom_positions(keys[i:i + 1], 1 << 20, 4)[0]
+            while srv.submit_write(t, int(b1[0]), int(b2[0]), msg[i % 64], i, pos, ta) == talekpir.EAGAIN:
+                time.sleep(0.0001)
+        else:
+            while srv.submit_read(t, reqs[t][i % 64], outs[i], i, ta) == talekpir.EAGAIN:
+                time.sleep(0.0001)
+    srv.drain()
+    th.join()
+    st = srv.stats()
+    out = {"offered_reads_per_s": rate * 0.9, "reads_per_s": st.reads_per_s, "p50_ms": st.p50_ms,
+           "p99_ms": st.p99_ms, "max_ms": st.max_ms, "reads": st.reads_done,
+           "writes": st.writes_done, "failed": st.failed, "launches": st.launches,
+           "mean_batch": st.mean_batch, "tables": len(tids),
+           "table_bytes": int(sum(s * 4096 for s in sizes))}
+    srv.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

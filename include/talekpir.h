@@ -1,0 +1,228 @@
+/*
+ * talekpir.h -- C ABI of libtalekpir, a GB300 (sm_103a) engine for the
+ * server side of Talek's private messaging (arxiv 2001.08250).
+ *
+ * A server holds a blocked cuckoo hash table of n buckets, each of d slots of
+ * msg_bytes bytes (Sections 4.3 and 5.3).  A PIR read (Section 2, step 5)
+ * returns the XOR of every bucket whose bit is set in the client's request
+ * vector; every bucket is read for every request, whatever the bits are, so
+ * the server's memory accesses do not depend on the request.
+ *
+ * Naming: n is the number of BUCKETS (the paper calls it b; the paper's n is
+ * the number of stored messages).  row_bytes = d * msg_bytes is the size of a
+ * bucket and of one reply.
+ *
+ * Layouts (all little-endian, all contiguous):
+ *   table      n rows of row_bytes; slot j of bucket k starts at byte
+ *              k*row_bytes + j*msg_bytes.  An empty slot holds zero bytes.
+ *   req_bits   B rows of ceil(n/64) uint64 words; bucket k is bit (k % 64) of
+ *              word k / 64 of the row (LSB first).  Bits at positions >= n are
+ *              ignored.
+ *   out        B rows of row_bytes: row b is the reply to request row b.
+ *
+ * Conventions:
+ *   - The caller owns every request and output buffer; the library owns the
+ *     device tables.  Pointers named d_* are device pointers on the current
+ *     CUDA device; all others are host pointers.
+ *   - Every call returns a tpir_status, except the creators, which return NULL
+ *     and leave the reason in tpir_last_error() (per thread).
+ *   - On an error no output is written, except where stated.
+ *   - msg_bytes must be a positive multiple of 16; d is 1..64; n >= 1.
+ *   - One tpir_db is used from one host thread at a time.
+ */
+#ifndef TALEKPIR_H
+#define TALEKPIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TPIR_OK = 0,
+    TPIR_EINVAL = -1,    /* bad argument (size, pointer, bucket index) */
+    TPIR_ENOMEM = -2,    /* device allocation failed or HBM budget exceeded */
+    TPIR_EFULL = -3,     /* cuckoo eviction bound hit; table rolled back */
+    TPIR_EAGAIN = -4,    /* serve queue full; try again */
+    TPIR_ETIMEDOUT = -5, /* a bounded wait inside a kernel gave up */
+    TPIR_ECUDA = -6,     /* a CUDA runtime call failed */
+    TPIR_ESHUTDOWN = -7  /* server is shutting down */
+} tpir_status;
+
+typedef struct tpir_db tpir_db;
+
+/* Version string of the library. */
+const char *tpir_version(void);
+/* Status of the last failed creator call on this thread. */
+tpir_status tpir_last_error(void);
+/* Human-readable name of a status code (static string). */
+const char *tpir_strerror(tpir_status s);
+
+/* ---- tables (Sections 4.3, 5.3; Fig. "Talek Variables") ------------------
+ * tpir_db_create allocates an all-zero table of n buckets x d slots x
+ * msg_bytes on the current device, 256-byte aligned, plus its host-side
+ * cuckoo metadata.  Returns NULL on error (EINVAL, ENOMEM, ECUDA). */
+tpir_db *tpir_db_create(uint64_t n, uint32_t d, uint32_t msg_bytes);
+void tpir_db_destroy(tpir_db *db);
+
+/* Shape and state: any output pointer may be NULL.  *d_table is the device
+ * address of the table; *epoch counts the writes applied so far. */
+tpir_status tpir_db_info(const tpir_db *db, uint64_t *n, uint32_t *d, uint32_t *msg_bytes,
+                         const void **d_table, uint64_t *epoch);
+
+/* Cuckoo policy (Section 5.3): keep at most `capacity` messages, collecting
+ * the oldest first (0 = never collect); give up an eviction walk after
+ * `max_evictions` evictions; s_cuckoo seeds the random choices (splitmix64),
+ * so that replicas given the same writes in the same order agree.
+ * Defaults: 0, 500, 0.  Only allowed while the table holds no item. */
+tpir_status tpir_db_set_policy(tpir_db *db, uint64_t capacity, uint32_t max_evictions,
+                               uint64_t s_cuckoo);
+
+/* Bulk payload load/dump of the whole table (bytes = n*row_bytes), from/to a
+ * host buffer.  Load replaces the payload and forgets all cuckoo metadata (the
+ * table is then read-only content for the write path's purposes: later writes
+ * treat every slot as free).  Synchronous. */
+tpir_status tpir_db_load(tpir_db *db, const void *host_table, size_t bytes);
+tpir_status tpir_db_dump(tpir_db *db, void *host_table, size_t bytes);
+
+/* ---- writes (Section 5.3, server steps 1-4) ------------------------------
+ * Inserts msg (msg_bytes, host) with candidate buckets b1, b2 < n: collects
+ * the oldest message if the table is at capacity, places the message in the
+ * lowest free slot of b1, else of b2, else walks evictions from a bucket
+ * chosen with s_cuckoo's randomness.  The placement is computed on the host
+ * (metadata only); the slot moves and the payload write run on the device in
+ * the db's stream order, after every read submitted before this call and
+ * before every read submitted after it.  Returns EFULL (nothing changed; the
+ * random draws stay consumed) when the walk exceeds max_evictions.
+ * *evictions_out (may be NULL) = evictions made. */
+tpir_status tpir_write(tpir_db *db, uint64_t b1, uint64_t b2, const void *msg,
+                       uint32_t *evictions_out);
+
+/* `count` writes in order, as if by `count` tpir_write calls, with one
+ * host-to-device copy and one move kernel: b1, b2 (count words), msgs
+ * (count x msg_bytes), all host.  status_out[i] / evictions_out[i] (may be
+ * NULL) receive each write's result; the call returns TPIR_OK unless a
+ * CUDA/allocation failure stopped it (then nothing was applied on the device). */
+tpir_status tpir_write_batch(tpir_db *db, uint32_t count, const uint64_t *b1, const uint64_t *b2,
+                             const void *msgs, tpir_status *status_out, uint32_t *evictions_out);
+
+/* ---- PIR reads (Section 2 step 5; batching as in Section 9.2) -------------
+ * Synchronous: req_bits (host, B rows) in, out (host, B x row_bytes) out.
+ * B = 0 is a no-op.  Sees every write made before the call. */
+tpir_status tpir_read_batch(tpir_db *db, const uint64_t *req_bits, uint32_t B, void *out);
+
+/* Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream):
+ * d_req_bits and d_out are device buffers that must stay valid until the
+ * stream reaches this point.  d_out must not overlap d_req_bits or the table.
+ * Ordered after all writes already made on this db. */
+tpir_status tpir_read_batch_async(tpir_db *db, const uint64_t *d_req_bits, uint32_t B,
+                                  void *d_out, void *stream);
+
+/* Force a kernel choice for tests and benchmarks: 0 = automatic (the tuned
+ * plan), 1 = plain streaming kernel (B <= 4 per launch, larger B is split into
+ * launches), 2 = batched register-tiled kernel. */
+tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
+
+/* Many tables in ONE persistent launch (the uneven-batching workload): job i
+ * reads B_i rows of d_req_bits_i against db_i into d_out_i.  Tables may differ
+ * in n, d and msg_bytes.  Up to TPIR_MAX_JOBS jobs per call. */
+#define TPIR_MAX_JOBS 128
+typedef struct {
+    tpir_db *db;
+    uint32_t B;
+    const uint64_t *d_req_bits;
+    void *d_out;
+} tpir_read_job;
+tpir_status tpir_read_multi_async(const tpir_read_job *jobs, uint32_t njobs, void *stream);
+
+/* Reads and clears the device-side status word that bounded waits inside the
+ * kernels set when they give up (TPIR_OK or TPIR_ETIMEDOUT). Synchronises the
+ * device. */
+tpir_status tpir_device_status(void);
+
+/* ---- private notifications (Section 7) ----------------------------------
+ * The global interest vector of a db: m_bits bits, k positions per write, the
+ * OR of the `window` most recent deltas; each delta summarises
+ * writes_per_delta writes (0 = a single delta that is never replaced), and a
+ * new delta opens, in place of the oldest, at the first write that finds the
+ * current one complete.  Kept on the device. */
+tpir_status tpir_bloom_create(tpir_db *db, uint64_t m_bits, uint32_t k, uint32_t window,
+                              uint32_t writes_per_delta);
+/* One write's interest vector given as its k bit positions (host, each < m). */
+tpir_status tpir_bloom_insert(tpir_db *db, const uint64_t *positions);
+/* `count` writes at once: positions is count x k (host). */
+tpir_status tpir_bloom_insert_batch(tpir_db *db, const uint64_t *positions, uint32_t count);
+/* One write's interest vector given whole (ceil(m/64) words, host); bits >= m
+ * are ignored. */
+tpir_status tpir_bloom_or_vector(tpir_db *db, const uint64_t *vec);
+/* GetUpdates: the global interest vector, ceil(m/64) words (host). */
+tpir_status tpir_bloom_get(tpir_db *db, uint64_t *out_words);
+
+/* ---- serving: continuous batching over resident tables -------------------
+ * A server thread admits reads and writes as they arrive, keeps tables
+ * resident under an HBM budget, applies each table's writes in arrival order,
+ * and launches the waiting reads of all tables together in one persistent
+ * launch per tick; up to max_inflight launches overlap on the device.  A read
+ * sees every write to its table admitted before the launch that serves it;
+ * its completion reports that write count (epoch). */
+typedef struct tpir_server tpir_server;
+
+typedef struct {
+    uint64_t hbm_budget_bytes; /* tables + staging must fit; 0 = 64 GiB */
+    uint32_t max_batch;        /* reads per table per launch (<= 1024); 0 = 256 */
+    uint32_t max_inflight;     /* launches in flight (1..8); 0 = 3 */
+    uint32_t queue_capacity;   /* admitted, unfinished ops; 0 = 65536 */
+    uint32_t tick_us;          /* batching interval; 0 = 200 */
+} tpir_serve_config;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;    /* tpir_status of the op */
+    uint32_t kind;     /* 0 = read, 1 = write */
+    uint32_t table_id;
+    uint32_t evictions;
+    uint64_t epoch;    /* writes to the table that the read saw / the write's number */
+    int64_t t_arrive_ns, t_launch_ns, t_done_ns; /* CLOCK_MONOTONIC */
+} tpir_completion;
+
+typedef struct {
+    uint64_t reads_done, writes_done, rejected, failed;
+    uint64_t launches;
+    double reads_per_s;               /* since the first admitted read */
+    double p50_ms, p99_ms, max_ms;    /* read latency, arrival to completion */
+    double mean_batch;                /* reads per table per launch */
+    uint64_t hbm_bytes_in_use;
+    uint64_t eviction_hist[8];        /* 0, 1, 2-3, 4-7, ..., >= 64 */
+} tpir_stats;
+
+tpir_status tpir_serve_create(const tpir_serve_config *cfg, tpir_server **out);
+/* Adds an all-zero table; ENOMEM if it does not fit in the budget. */
+tpir_status tpir_serve_add_table(tpir_server *s, uint64_t n, uint32_t d, uint32_t msg_bytes,
+                                 uint32_t *table_id);
+/* The db of a table, e.g. to load its payload or set its policy before serving. */
+tpir_status tpir_serve_table(tpir_server *s, uint32_t table_id, tpir_db **db);
+/* Enqueue a read: req_bits (host, one row) is copied at once; out (host,
+ * row_bytes) is written before the completion is reported.  t_arrive_ns = the
+ * arrival time to measure latency from (0 = now).  EAGAIN if the queue is full. */
+tpir_status tpir_serve_submit_read(tpir_server *s, uint32_t table_id, const uint64_t *req_bits,
+                                   void *out, uint64_t tag, int64_t t_arrive_ns);
+/* Enqueue a write (copied at once); bloom_positions (k words, may be NULL)
+ * are OR-ed into the table's interest vector if it has one. */
+tpir_status tpir_serve_submit_write(tpir_server *s, uint32_t table_id, uint64_t b1, uint64_t b2,
+                                    const void *msg, const uint64_t *bloom_positions, uint64_t tag,
+                                    int64_t t_arrive_ns);
+/* Completed ops, oldest first; *ndone <= max. */
+tpir_status tpir_serve_poll(tpir_server *s, tpir_completion *done, uint32_t max, uint32_t *ndone);
+/* Blocks until every admitted op has completed. */
+tpir_status tpir_serve_drain(tpir_server *s);
+tpir_status tpir_serve_stats(tpir_server *s, tpir_stats *st);
+tpir_status tpir_serve_reset_stats(tpir_server *s);
+/* Stops admitting (later submits return ESHUTDOWN), drains, frees everything. */
+tpir_status tpir_serve_destroy(tpir_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TALEKPIR_H */

@@ -1,0 +1,584 @@
+// C ABI of libtalekpir: tables, PIR reads, cuckoo writes, interest vectors.
+// Every step of a read or write runs in this library's kernels; the host code
+// here validates arguments, plans launches, moves buffers and keeps the
+// cuckoo metadata.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "tpir_internal.h"
+
+namespace {
+thread_local tpir_status g_last = TPIR_OK;
+constexpr uint32_t kPlainMaxB = 4;
+}  // namespace
+
+namespace tpir {
+
+tpir_status set_error(tpir_status s) {
+  g_last = s;
+  return s;
+}
+
+tpir_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TPIR_OK;
+  if (e == cudaErrorMemoryAllocation) return TPIR_ENOMEM;
+  return TPIR_ECUDA;
+}
+
+uint64_t db_device_bytes(uint64_t n, uint32_t d, uint32_t z) {
+  return n * static_cast<uint64_t>(d) * z;
+}
+
+bool grow_dev(void** p, uint64_t* cap, uint64_t need) {
+  if (*cap >= need) return true;
+  uint64_t c = std::max<uint64_t>(need, *cap * 2);
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, c) != cudaSuccess) {
+    *p = nullptr;
+    return false;
+  }
+  *cap = c;
+  return true;
+}
+
+bool grow_pinned(void** p, uint64_t* cap, uint64_t need) {
+  if (*cap >= need) return true;
+  uint64_t c = std::max<uint64_t>(need, *cap * 2);
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMallocHost(p, c) != cudaSuccess) {
+    *p = nullptr;
+    return false;
+  }
+  *cap = c;
+  return true;
+}
+
+void order_after_writes(tpir_db* db, cudaStream_t st) {
+  if (db->epoch > 0 || db->last_write) cudaStreamWaitEvent(st, db->last_write, 0);
+}
+
+void note_read(tpir_db* db, cudaStream_t st) {
+  if (st == db->stream) return;  // same stream: ordered already
+  for (auto& pr : db->read_events) {
+    if (pr.first == st) {
+      cudaEventRecord(pr.second, st);
+      return;
+    }
+  }
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return;
+  cudaEventRecord(ev, st);
+  db->read_events.emplace_back(st, ev);
+}
+
+// Writes go on `st` after every read already submitted on other streams.
+void order_writes_after_reads(tpir_db* db, cudaStream_t st) {
+  for (auto& pr : db->read_events)
+    if (pr.first != st) cudaStreamWaitEvent(st, pr.second, 0);
+}
+
+// ---- launch planning -------------------------------------------------------
+
+// Per-row cost of one item of a job, in SM clocks: the larger of its LOP3
+// work (64 per SM per clock) and its table bytes (HBM share per SM).
+static double row_cost(const ScanJob& j) {
+  const Shape& s = j.shape;
+  const double alu = static_cast<double>(s.bt()) * s.wt() / 64.0;
+  const double mem = static_cast<double>(std::min<uint32_t>(s.wt(), j.Wd)) * 4.0 / 24.0;
+  return std::max(alu, mem) + 8.0;
+}
+
+// Chooses kc_rows for one job so that items fill `grid` CTAs with the least
+// makespan (rounds of items x rows per item).
+static void plan_single(ScanJob& j, int grid) {
+  const uint32_t sr = j.shape.srows();
+  const uint64_t tiles = static_cast<uint64_t>((j.B + j.shape.bt() - 1) / j.shape.bt()) *
+                         ((j.Wd + j.shape.wt() - 1) / j.shape.wt());
+  const uint64_t max_kc = std::max<uint64_t>(1, (j.n + sr - 1) / sr);
+  const uint64_t hi = std::min<uint64_t>(max_kc, static_cast<uint64_t>(grid) * 4 / std::max<uint64_t>(1, tiles) + 2);
+  double best = 1e300;
+  uint32_t best_rows = 0;
+  for (uint64_t nkc = 1; nkc <= hi; ++nkc) {
+    uint64_t rows = (j.n + nkc - 1) / nkc;
+    rows = (rows + sr - 1) / sr * sr;
+    const uint64_t items = tiles * ((j.n + rows - 1) / rows);
+    const uint64_t rounds = (items + grid - 1) / grid;
+    const double cost = static_cast<double>(rounds) * (static_cast<double>(rows) + 32.0) +
+                        1e-6 * static_cast<double>(items);
+    if (cost < best) {
+      best = cost;
+      best_rows = static_cast<uint32_t>(std::min<uint64_t>(rows, 0xFFFFFFF0ull));
+    }
+  }
+  j.kc_rows = best_rows;
+}
+
+static ScanJob make_job(const tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out) {
+  ScanJob j{};
+  j.T = reinterpret_cast<const uint32_t*>(db->d_table);
+  j.R = d_req;
+  j.out = reinterpret_cast<uint32_t*>(d_out);
+  j.n = db->n;
+  j.Wd = db->Wd;
+  j.words64 = db->words64;
+  j.B = B;
+  j.shape = choose_shape(db->Wd, B);
+  return j;
+}
+
+static int batched_grid() { return device_sm_count() * batched_ctas_per_sm(); }
+
+tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
+                         cudaStream_t st) {
+  if (B == 0) return TPIR_OK;
+  order_after_writes(db, st);
+  int kernel = db->forced_kernel;
+  if (kernel == 0) kernel = (B <= kPlainMaxB) ? 1 : 2;
+  cudaError_t e = cudaSuccess;
+  if (kernel == 1) {
+    const uint32_t* T = reinterpret_cast<const uint32_t*>(db->d_table);
+    for (uint32_t b0 = 0; b0 < B && e == cudaSuccess; b0 += kPlainMaxB) {
+      const uint32_t nb = std::min(kPlainMaxB, B - b0);
+      e = launch_plain(T, db->n, db->Wd, d_req + static_cast<uint64_t>(b0) * db->words64,
+                       db->words64, nb,
+                       reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_out) +
+                                                   static_cast<uint64_t>(b0) * db->row_bytes),
+                       st, 0);
+    }
+  } else {
+    ScanLaunch L;
+    L.njobs = 1;
+    ScanJob j = make_job(db, d_req, B, d_out);
+    const int grid = batched_grid();
+    plan_single(j, grid);
+    j.item_begin = 0;
+    if (!finalize_job(j)) return TPIR_EINVAL;
+    L.jobs[0] = j;
+    L.total_items = j.n_bt * j.n_wt * j.n_kc;
+    e = launch_zero_outputs(L, st);
+    if (e == cudaSuccess)
+      e = launch_batched(L, static_cast<int>(std::min<uint64_t>(L.total_items, grid)), st);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  note_read(db, st);
+  return TPIR_OK;
+}
+
+tpir_status apply_writes_core(tpir_db* db, uint32_t count, const uint64_t* b1, const uint64_t* b2,
+                              const uint8_t* msgs, tpir_status* st_out, uint32_t* ev_out,
+                              cudaStream_t st, tpir_write_staging& stg) {
+  if (count == 0) return TPIR_OK;
+  std::vector<MoveOp> ops;
+  ops.reserve(count * 2);
+  const uint64_t z = db->z;
+  uint32_t ok = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    uint32_t ev = 0;
+    const tpir_status s = db->meta->insert(b1[i], b2[i], i, ops, &ev);
+    if (st_out) st_out[i] = s;
+    if (ev_out) ev_out[i] = ev;
+    if (s == TPIR_OK) ++ok;
+  }
+  if (!ops.empty()) {
+    const uint64_t pay_bytes = count * z;
+    const uint64_t ops_bytes = ops.size() * sizeof(MoveOp);
+    if (!grow_pinned(reinterpret_cast<void**>(&stg.h), &stg.h_cap, pay_bytes + ops_bytes) ||
+        !grow_dev(reinterpret_cast<void**>(&stg.d_payload), &stg.pay_cap, pay_bytes) ||
+        !grow_dev(reinterpret_cast<void**>(&stg.d_ops), &stg.ops_cap, ops_bytes))
+      return TPIR_ENOMEM;
+    std::memcpy(stg.h, msgs, pay_bytes);
+    std::memcpy(stg.h + pay_bytes, ops.data(), ops_bytes);
+    cudaError_t e = cudaMemcpyAsync(stg.d_payload, stg.h, pay_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(stg.d_ops, stg.h + pay_bytes, ops_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = launch_apply_moves(db->d_table, db->z, stg.d_ops, static_cast<uint32_t>(ops.size()),
+                             stg.d_payload, db->d_tmp, st);
+    if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  db->epoch += ok;
+  return TPIR_OK;
+}
+
+// Positions of `count` writes (k each) into the current delta, opening new
+// deltas (in place of the oldest) whenever the current one is complete.
+tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, cudaStream_t st,
+                              tpir_write_staging& stg) {
+  tpir_bloom_state& bl = db->bloom;
+  if (!bl.d_deltas) return TPIR_EINVAL;
+  for (uint64_t i = 0; i < static_cast<uint64_t>(count) * bl.k; ++i)
+    if (pos[i] >= bl.m) return TPIR_EINVAL;
+  const uint64_t bytes = static_cast<uint64_t>(count) * bl.k * 8;
+  if (!grow_pinned(reinterpret_cast<void**>(&stg.h), &stg.h_cap, bytes) ||
+      !grow_dev(reinterpret_cast<void**>(&stg.d_pos), &stg.pos_cap, bytes))
+    return TPIR_ENOMEM;
+  std::memcpy(stg.h, pos, bytes);
+  cudaError_t e = cudaMemcpyAsync(stg.d_pos, stg.h, bytes, cudaMemcpyHostToDevice, st);
+  uint32_t i = 0;
+  while (e == cudaSuccess && i < count) {
+    if (bl.per_delta && bl.count == bl.per_delta) {
+      bl.cur = (bl.cur + 1) % bl.window;
+      bl.count = 0;
+      e = cudaMemsetAsync(bl.d_deltas + static_cast<uint64_t>(bl.cur) * bl.words, 0,
+                          bl.words * 8, st);
+      if (e != cudaSuccess) break;
+    }
+    uint32_t seg = count - i;
+    if (bl.per_delta) seg = std::min(seg, bl.per_delta - bl.count);
+    e = launch_bloom_set(bl.d_deltas + static_cast<uint64_t>(bl.cur) * bl.words,
+                         stg.d_pos + static_cast<uint64_t>(i) * bl.k,
+                         static_cast<uint64_t>(seg) * bl.k, st);
+    bl.count += seg;
+    i += seg;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
+  return cuda_status(e);
+}
+
+tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st) {
+  ScanLaunch L;
+  L.njobs = 0;
+  const int grid = batched_grid();
+  // shapes first, then k-chunks sized so that items cost about the same
+  std::vector<ScanJob> js;
+  double total = 0.0;
+  for (uint32_t i = 0; i < njobs; ++i) {
+    const tpir_read_job& q = jobs[i];
+    if (!q.db || (q.B && (!q.d_req_bits || !q.d_out))) return TPIR_EINVAL;
+    if (q.B == 0) continue;
+    if ((reinterpret_cast<uintptr_t>(q.d_out) & 15) || (reinterpret_cast<uintptr_t>(q.d_req_bits) & 7))
+      return TPIR_EINVAL;
+    ScanJob j = make_job(q.db, q.d_req_bits, q.B, q.d_out);
+    const double tiles = static_cast<double>((j.B + j.shape.bt() - 1) / j.shape.bt()) *
+                         ((j.Wd + j.shape.wt() - 1) / j.shape.wt());
+    total += tiles * static_cast<double>(j.n) * row_cost(j);
+    js.push_back(j);
+  }
+  if (js.empty()) return TPIR_OK;
+  const double target = total / (static_cast<double>(grid) * 4.0);
+  uint32_t items = 0;
+  for (auto& j : js) {
+    const uint32_t sr = j.shape.srows();
+    const double rc = row_cost(j);
+    uint64_t rows = static_cast<uint64_t>(target / rc);
+    rows = std::max<uint64_t>(sr, (rows + sr - 1) / sr * sr);
+    const uint64_t nmax = (j.n + sr - 1) / sr * sr;
+    j.kc_rows = static_cast<uint32_t>(std::min<uint64_t>(rows, std::min<uint64_t>(nmax, 0xFFFFFFF0ull)));
+    if (!finalize_job(j)) return TPIR_EINVAL;
+    j.item_begin = items;
+    items += j.n_bt * j.n_wt * j.n_kc;
+    L.jobs[L.njobs++] = j;
+  }
+  L.total_items = items;
+  cudaError_t e = launch_zero_outputs(L, st);
+  if (e == cudaSuccess) e = launch_batched(L, static_cast<int>(std::min<uint32_t>(items, grid)), st);
+  return cuda_status(e);
+}
+
+void tpir_write_staging_release(tpir_write_staging& s) {
+  if (s.h) cudaFreeHost(s.h);
+  cudaFree(s.d_payload);
+  cudaFree(s.d_ops);
+  cudaFree(s.d_pos);
+  s = tpir_write_staging();
+}
+
+}  // namespace tpir
+
+using namespace tpir;
+
+void tpir_write_staging::release() { tpir::tpir_write_staging_release(*this); }
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* tpir_version(void) { return "libtalekpir 0.1 (sm_103a)"; }
+
+tpir_status tpir_last_error(void) { return g_last; }
+
+const char* tpir_strerror(tpir_status s) {
+  switch (s) {
+    case TPIR_OK: return "ok";
+    case TPIR_EINVAL: return "invalid argument";
+    case TPIR_ENOMEM: return "out of device memory or HBM budget";
+    case TPIR_EFULL: return "cuckoo table full: eviction bound hit";
+    case TPIR_EAGAIN: return "queue full, try again";
+    case TPIR_ETIMEDOUT: return "bounded device wait timed out";
+    case TPIR_ECUDA: return "CUDA runtime error";
+    case TPIR_ESHUTDOWN: return "server shut down";
+  }
+  return "unknown status";
+}
+
+tpir_db* tpir_db_create(uint64_t n, uint32_t d, uint32_t msg_bytes) {
+  if (n == 0 || d == 0 || d > 64 || msg_bytes == 0 || (msg_bytes % 16) != 0 ||
+      static_cast<uint64_t>(d) * msg_bytes > (1ull << 30) || n > (1ull << 40)) {
+    set_error(TPIR_EINVAL);
+    return nullptr;
+  }
+  tpir_db* db = new (std::nothrow) tpir_db();
+  if (!db) {
+    set_error(TPIR_ENOMEM);
+    return nullptr;
+  }
+  db->n = n;
+  db->d = d;
+  db->z = msg_bytes;
+  db->row_bytes = d * msg_bytes;
+  db->Wd = db->row_bytes / 4;
+  db->words64 = static_cast<uint32_t>((n + 63) / 64);
+  cudaGetDevice(&db->device);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&db->d_table), n * db->row_bytes);
+  if (e == cudaSuccess) e = cudaMemset(db->d_table, 0, n * db->row_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&db->d_tmp), msg_bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&db->last_write, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(db->last_write, db->stream);
+  if (e != cudaSuccess) {
+    set_error(cuda_status(e));
+    tpir_db_destroy(db);
+    return nullptr;
+  }
+  db->meta = new (std::nothrow) CuckooMeta(n, d);
+  if (!db->meta) {
+    set_error(TPIR_ENOMEM);
+    tpir_db_destroy(db);
+    return nullptr;
+  }
+  db->meta->set_policy(0, 500, 0);
+  return db;
+}
+
+void tpir_db_destroy(tpir_db* db) {
+  if (!db) return;
+  if (db->stream) cudaStreamSynchronize(db->stream);
+  for (auto& pr : db->read_events) {
+    cudaEventSynchronize(pr.second);
+    cudaEventDestroy(pr.second);
+  }
+  cudaFree(db->d_table);
+  db->stage.release();
+  cudaFree(db->d_tmp);
+  cudaFree(db->d_req);
+  cudaFree(db->d_out);
+  cudaFree(db->bloom.d_deltas);
+  cudaFree(db->bloom.d_out);
+  if (db->last_write) cudaEventDestroy(db->last_write);
+  if (db->stream) cudaStreamDestroy(db->stream);
+  delete db->meta;
+  delete db;
+}
+
+tpir_status tpir_db_info(const tpir_db* db, uint64_t* n, uint32_t* d, uint32_t* msg_bytes,
+                         const void** d_table, uint64_t* epoch) {
+  if (!db) return TPIR_EINVAL;
+  if (n) *n = db->n;
+  if (d) *d = db->d;
+  if (msg_bytes) *msg_bytes = db->z;
+  if (d_table) *d_table = db->d_table;
+  if (epoch) *epoch = db->epoch;
+  return TPIR_OK;
+}
+
+tpir_status tpir_db_set_policy(tpir_db* db, uint64_t capacity, uint32_t max_evictions,
+                               uint64_t s_cuckoo) {
+  if (!db) return TPIR_EINVAL;
+  if (db->meta->live() != 0) return TPIR_EINVAL;
+  db->meta->set_policy(capacity, max_evictions, s_cuckoo);
+  return TPIR_OK;
+}
+
+tpir_status tpir_db_set_kernel(tpir_db* db, int kernel) {
+  if (!db || kernel < 0 || kernel > 2) return TPIR_EINVAL;
+  db->forced_kernel = kernel;
+  return TPIR_OK;
+}
+
+tpir_status tpir_db_load(tpir_db* db, const void* host_table, size_t bytes) {
+  if (!db || !host_table || bytes != db->n * db->row_bytes) return TPIR_EINVAL;
+  cudaError_t e = cudaEventSynchronize(db->last_write);
+  if (e != cudaSuccess) return cuda_status(e);
+  order_writes_after_reads(db, db->stream);
+  e = cudaMemcpyAsync(db->d_table, host_table, bytes, cudaMemcpyHostToDevice, db->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(db->last_write, db->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  db->meta->clear();
+  return TPIR_OK;
+}
+
+tpir_status tpir_db_dump(tpir_db* db, void* host_table, size_t bytes) {
+  if (!db || !host_table || bytes != db->n * db->row_bytes) return TPIR_EINVAL;
+  order_writes_after_reads(db, db->stream);
+  cudaError_t e =
+      cudaMemcpyAsync(host_table, db->d_table, bytes, cudaMemcpyDeviceToHost, db->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  return cuda_status(e);
+}
+
+tpir_status tpir_write(tpir_db* db, uint64_t b1, uint64_t b2, const void* msg,
+                       uint32_t* evictions_out) {
+  if (!db || !msg) return TPIR_EINVAL;
+  tpir_status s = TPIR_OK;
+  uint32_t ev = 0;
+  tpir_status r = tpir_write_batch(db, 1, &b1, &b2, msg, &s, &ev);
+  if (evictions_out) *evictions_out = ev;
+  return r != TPIR_OK ? r : s;
+}
+
+tpir_status tpir_write_batch(tpir_db* db, uint32_t count, const uint64_t* b1, const uint64_t* b2,
+                             const void* msgs, tpir_status* status_out, uint32_t* evictions_out) {
+  if (!db || (count && (!b1 || !b2 || !msgs))) return TPIR_EINVAL;
+  if (count == 0) return TPIR_OK;
+  // the staging of the previous call must have been consumed
+  cudaError_t e = cudaEventSynchronize(db->last_write);
+  if (e != cudaSuccess) return cuda_status(e);
+  order_writes_after_reads(db, db->stream);
+  return apply_writes_core(db, count, b1, b2, static_cast<const uint8_t*>(msgs), status_out,
+                           evictions_out, db->stream, db->stage);
+}
+
+tpir_status tpir_read_batch(tpir_db* db, const uint64_t* req_bits, uint32_t B, void* out) {
+  if (!db) return TPIR_EINVAL;
+  if (B == 0) return TPIR_OK;
+  if (!req_bits || !out) return TPIR_EINVAL;
+  const uint64_t rb = static_cast<uint64_t>(B) * db->words64 * 8;
+  const uint64_t ob = static_cast<uint64_t>(B) * db->row_bytes;
+  if (!grow_dev(reinterpret_cast<void**>(&db->d_req), &db->req_cap, rb) ||
+      !grow_dev(reinterpret_cast<void**>(&db->d_out), &db->out_cap, ob))
+    return TPIR_ENOMEM;
+  cudaError_t e = cudaMemcpyAsync(db->d_req, req_bits, rb, cudaMemcpyHostToDevice, db->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  tpir_status s = enqueue_read(db, db->d_req, B, db->d_out, db->stream);
+  if (s != TPIR_OK) return s;
+  e = cudaMemcpyAsync(out, db->d_out, ob, cudaMemcpyDeviceToHost, db->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = 0;
+  if (read_device_status_and_clear(&st) != 0) return TPIR_ECUDA;
+  return st ? static_cast<tpir_status>(st) : TPIR_OK;
+}
+
+tpir_status tpir_read_batch_async(tpir_db* db, const uint64_t* d_req_bits, uint32_t B,
+                                  void* d_out, void* stream) {
+  if (!db) return TPIR_EINVAL;
+  if (B == 0) return TPIR_OK;
+  if (!d_req_bits || !d_out) return TPIR_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 15) || (reinterpret_cast<uintptr_t>(d_req_bits) & 7))
+    return TPIR_EINVAL;
+  return enqueue_read(db, d_req_bits, B, d_out, static_cast<cudaStream_t>(stream));
+}
+
+tpir_status tpir_read_multi_async(const tpir_read_job* jobs, uint32_t njobs, void* stream) {
+  if (njobs == 0) return TPIR_OK;
+  if (!jobs || njobs > TPIR_MAX_JOBS) return TPIR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (uint32_t i = 0; i < njobs; ++i)
+    if (!jobs[i].db) return TPIR_EINVAL;
+  for (uint32_t i = 0; i < njobs; ++i)
+    if (jobs[i].B) order_after_writes(jobs[i].db, st);
+  tpir_status s = enqueue_multi(jobs, njobs, st);
+  if (s != TPIR_OK) return s;
+  for (uint32_t i = 0; i < njobs; ++i)
+    if (jobs[i].B) note_read(jobs[i].db, st);
+  return TPIR_OK;
+}
+
+tpir_status tpir_device_status(void) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = 0;
+  if (read_device_status_and_clear(&st) != 0) return TPIR_ECUDA;
+  return st ? static_cast<tpir_status>(st) : TPIR_OK;
+}
+
+// ---- Bloom -----------------------------------------------------------------
+tpir_status tpir_bloom_create(tpir_db* db, uint64_t m_bits, uint32_t k, uint32_t window,
+                              uint32_t writes_per_delta) {
+  if (!db || m_bits == 0 || k == 0 || window == 0 || m_bits > (1ull << 36)) return TPIR_EINVAL;
+  tpir_bloom_state& bl = db->bloom;
+  cudaFree(bl.d_deltas);
+  cudaFree(bl.d_out);
+  bl.d_deltas = nullptr;
+  bl.d_out = nullptr;
+  bl.m = m_bits;
+  bl.words = (m_bits + 63) / 64;
+  bl.k = k;
+  bl.window = window;
+  bl.per_delta = writes_per_delta;
+  bl.cur = 0;
+  bl.count = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&bl.d_deltas), bl.words * 8 * window);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&bl.d_out), bl.words * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bl.d_deltas, 0, bl.words * 8 * window, db->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  if (e != cudaSuccess) {
+    cudaFree(bl.d_deltas);
+    cudaFree(bl.d_out);
+    bl.d_deltas = nullptr;
+    bl.d_out = nullptr;
+    return cuda_status(e);
+  }
+  return TPIR_OK;
+}
+
+tpir_status tpir_bloom_insert(tpir_db* db, const uint64_t* positions) {
+  return tpir_bloom_insert_batch(db, positions, 1);
+}
+
+tpir_status tpir_bloom_insert_batch(tpir_db* db, const uint64_t* positions, uint32_t count) {
+  if (!db || (count && !positions)) return TPIR_EINVAL;
+  if (count == 0) return TPIR_OK;
+  cudaError_t e = cudaEventSynchronize(db->last_write);
+  if (e != cudaSuccess) return cuda_status(e);
+  order_writes_after_reads(db, db->stream);
+  return bloom_insert_core(db, positions, count, db->stream, db->stage);
+}
+
+tpir_status tpir_bloom_or_vector(tpir_db* db, const uint64_t* vec) {
+  if (!db || !vec || !db->bloom.d_deltas) return TPIR_EINVAL;
+  tpir_bloom_state& bl = db->bloom;
+  cudaError_t e = cudaEventSynchronize(db->last_write);
+  if (e != cudaSuccess) return cuda_status(e);
+  const uint64_t bytes = bl.words * 8;
+  if (!grow_pinned(reinterpret_cast<void**>(&db->stage.h), &db->stage.h_cap, bytes) ||
+      !grow_dev(reinterpret_cast<void**>(&db->stage.d_pos), &db->stage.pos_cap, bytes))
+    return TPIR_ENOMEM;
+  std::memcpy(db->stage.h, vec, bytes);
+  order_writes_after_reads(db, db->stream);
+  if (bl.per_delta && bl.count == bl.per_delta) {
+    bl.cur = (bl.cur + 1) % bl.window;
+    bl.count = 0;
+    e = cudaMemsetAsync(bl.d_deltas + static_cast<uint64_t>(bl.cur) * bl.words, 0, bytes,
+                        db->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(db->stage.d_pos, db->stage.h, bytes, cudaMemcpyHostToDevice, db->stream);
+  if (e == cudaSuccess)
+    e = launch_bloom_or(bl.d_deltas + static_cast<uint64_t>(bl.cur) * bl.words, db->stage.d_pos,
+                        bl.m, db->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(db->last_write, db->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  bl.count += 1;
+  return TPIR_OK;
+}
+
+tpir_status tpir_bloom_get(tpir_db* db, uint64_t* out_words) {
+  if (!db || !out_words || !db->bloom.d_deltas) return TPIR_EINVAL;
+  tpir_bloom_state& bl = db->bloom;
+  cudaError_t e = launch_bloom_union(bl.d_deltas, bl.window, bl.words, bl.d_out, db->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_words, bl.d_out, bl.words * 8, cudaMemcpyDeviceToHost, db->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  return cuda_status(e);
+}
+
+}  // extern "C"

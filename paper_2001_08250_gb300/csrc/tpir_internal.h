@@ -1,0 +1,197 @@
+// Internal declarations of libtalekpir (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/talekpir.h"
+
+namespace tpir {
+
+// ---------------------------------------------------------------------------
+// Batched scan (register-tiled GF(2) product), one persistent launch over a
+// list of jobs.  Each job is cut into items = (B-tile, W-tile, k-chunk).
+// ---------------------------------------------------------------------------
+constexpr int kConsumerWarps = 8;                    // compute warps per CTA
+constexpr int kScanThreads = 32 * (kConsumerWarps + 1);  // + 1 producer warp
+constexpr int kMR = 8;                               // requests per thread
+constexpr int kNW = 16;                              // 32-bit words per thread
+constexpr int kStages = 5;                           // smem pipeline depth
+constexpr int kStageBytes = 20 * 1024;               // table tile + masks, per stage
+constexpr int kScanSmem = kStages * kStageBytes + 256;
+
+// Warp layout of a CTA tile: LW lanes along the row (W), 32/LW lanes along
+// the requests; WB warps along requests, WW along W and WK along buckets
+// (WB * WW * WK = 8).  Warps along buckets take alternate rows of each stage
+// and XOR-reduce their partials into the output at the end.
+struct Shape {
+  uint8_t lw_log2;     // 2..5
+  uint8_t wb;          // warps along B
+  uint8_t ww;          // warps along W
+  uint8_t wk;          // warps along k (buckets)
+  uint8_t srows_log2;  // rows (buckets) per pipeline stage
+  __host__ __device__ int lw() const { return 1 << lw_log2; }
+  __host__ __device__ int bt() const { return wb * (32 / lw()) * kMR; }  // requests per tile
+  __host__ __device__ int wt() const { return ww * lw() * kNW; }         // words per tile
+  __host__ __device__ int srows() const { return 1 << srows_log2; }
+};
+
+struct ScanJob {
+  const uint32_t* T;   // table, n rows of Wd words
+  const uint64_t* R;   // request bits, B rows of words64
+  uint32_t* out;       // B rows of Wd words (zeroed first when split)
+  uint64_t n;
+  uint32_t Wd;         // row length in 32-bit words (d*msg_bytes/4)
+  uint32_t words64;    // u64 words per request row
+  uint32_t B;
+  Shape shape;
+  uint32_t n_bt, n_wt, n_kc;
+  uint32_t kc_rows;    // buckets per k-chunk (multiple of 64)
+  uint32_t item_begin; // index of this job's first item in the launch
+  uint32_t split;      // partial replies are XOR-reduced (n_kc > 1 or wk > 1)
+};
+
+struct ScanLaunch {
+  uint32_t njobs;
+  uint32_t total_items;
+  ScanJob jobs[TPIR_MAX_JOBS];
+};
+
+// Fills a job's tiling from its shape/k-chunking and validates smem fit.
+bool finalize_job(ScanJob& j);
+Shape choose_shape(uint32_t Wd, uint32_t B);
+int scan_stage_bytes(const Shape& s);
+
+// Launch helpers (scan.cu).  All return cudaError_t of the launch.
+cudaError_t launch_batched(const ScanLaunch& L, int grid, cudaStream_t st);
+cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
+                         uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st, int ctas);
+cudaError_t launch_zero_outputs(const ScanLaunch& L, cudaStream_t st);
+int device_sm_count();
+int plain_ctas_per_sm();
+int batched_ctas_per_sm();
+
+// State kernels (state.cu)
+struct MoveOp {   // one step of a write's slot moves, executed in order
+  uint64_t dst;   // slot index (bucket*d + j), or kTmpSlot
+  uint64_t src;   // slot index, kTmpSlot, or payload index (kind 1)
+  uint32_t kind;  // 0 copy slot->slot, 1 payload->slot, 2 zero slot
+  uint32_t pad;
+};
+constexpr uint64_t kTmpSlot = ~0ull;
+cudaError_t launch_apply_moves(uint8_t* table, uint32_t z, const MoveOp* ops, uint32_t nops,
+                               const uint8_t* payloads, uint8_t* tmp, cudaStream_t st);
+cudaError_t launch_bloom_set(uint64_t* delta, const uint64_t* pos, uint64_t count, cudaStream_t st);
+cudaError_t launch_bloom_or(uint64_t* delta, const uint64_t* vec, uint64_t m, cudaStream_t st);
+cudaError_t launch_bloom_union(const uint64_t* deltas, uint32_t window, uint64_t words,
+                               uint64_t* out, cudaStream_t st);
+
+int read_device_status_and_clear(int* status);
+
+// Host cuckoo metadata (cuckoo.cpp): same placement rules as the paper's
+// Section 5.3 insertion; emits the device moves of one insertion.
+class CuckooMeta {
+ public:
+  CuckooMeta(uint64_t n, uint32_t d);
+  void set_policy(uint64_t capacity, uint32_t max_evictions, uint64_t seed);
+  void clear();
+  uint64_t live() const { return live_; }
+  // Returns TPIR_OK / TPIR_EINVAL / TPIR_EFULL; on OK appends the moves to
+  // `ops` (payload index `payload_idx` for the new message).
+  tpir_status insert(uint64_t b1, uint64_t b2, uint64_t payload_idx, std::vector<MoveOp>& ops,
+                     uint32_t* evictions);
+  uint64_t capacity() const { return capacity_; }
+  uint32_t max_evictions() const { return max_ev_; }
+
+ private:
+  static constexpr uint64_t kEmpty = ~0ull;
+  uint64_t n_;
+  uint32_t d_;
+  uint64_t capacity_ = 0;
+  uint32_t max_ev_ = 500;
+  uint64_t rng_ = 0;
+  std::vector<uint64_t> slot_item_;   // item seq held by each slot
+  std::vector<uint64_t> item_slot_;   // ring indexed by seq % ring
+  std::vector<uint64_t> item_b1_, item_b2_;
+  uint64_t head_ = 0, next_seq_ = 0, live_ = 0;
+  uint64_t ring_ = 0;
+  uint64_t next_rand();
+  int64_t lowest_free(uint64_t e) const;
+  uint64_t& islot(uint64_t seq) { return item_slot_[seq % ring_]; }
+};
+
+}  // namespace tpir
+
+// Host/device staging of one batch of writes (payloads, move list, Bloom
+// positions); reusable once the stream that consumed it has passed that point.
+struct tpir_write_staging {
+  uint8_t* h = nullptr;  // pinned
+  uint64_t h_cap = 0;
+  uint8_t* d_payload = nullptr;
+  uint64_t pay_cap = 0;
+  tpir::MoveOp* d_ops = nullptr;
+  uint64_t ops_cap = 0;
+  uint64_t* d_pos = nullptr;
+  uint64_t pos_cap = 0;
+  void release();
+};
+
+// The db object behind the opaque C handle.
+struct tpir_bloom_state {
+  uint64_t m = 0, words = 0;
+  uint32_t k = 0, window = 1, per_delta = 0;
+  uint32_t cur = 0, count = 0;
+  uint64_t* d_deltas = nullptr;   // window x words
+  uint64_t* d_out = nullptr;      // words
+};
+
+struct tpir_db {
+  uint64_t n = 0;
+  uint32_t d = 0, z = 0;
+  uint32_t row_bytes = 0, Wd = 0, words64 = 0;
+  int device = 0;
+  uint8_t* d_table = nullptr;
+  uint64_t epoch = 0;
+  int forced_kernel = 0;
+  cudaStream_t stream = nullptr;        // the db's own stream (writes, sync reads)
+  cudaEvent_t last_write = nullptr;     // recorded after each write
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> read_events;  // async reads per stream
+  tpir::CuckooMeta* meta = nullptr;
+  // write staging of the db's own API calls
+  tpir_write_staging stage;
+  uint8_t* d_tmp = nullptr;             // one slot: breaks cycles of slot moves
+  // sync read staging
+  uint64_t* d_req = nullptr;
+  uint8_t* d_out = nullptr;
+  uint64_t req_cap = 0, out_cap = 0;
+  tpir_bloom_state bloom;
+};
+
+namespace tpir {
+tpir_status set_error(tpir_status s);
+tpir_status cuda_status(cudaError_t e);
+// enqueue a read of db on stream (device buffers), honoring write ordering
+tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
+                         cudaStream_t st);
+// order stream `st` after the db's last write, and record a read event
+void order_after_writes(tpir_db* db, cudaStream_t st);
+void note_read(tpir_db* db, cudaStream_t st);
+// A batch of writes: host-side placement, device moves enqueued on `st`
+// using `stg` (which must be free); records db->last_write on `st`.
+tpir_status apply_writes_core(tpir_db* db, uint32_t count, const uint64_t* b1, const uint64_t* b2,
+                              const uint8_t* msgs, tpir_status* st_out, uint32_t* ev_out,
+                              cudaStream_t st, tpir_write_staging& stg);
+// Bloom positions of `count` writes, same staging contract.
+tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, cudaStream_t st,
+                              tpir_write_staging& stg);
+// Many jobs in one persistent launch (no cross-stream ordering done here).
+tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st);
+void order_writes_after_reads(tpir_db* db, cudaStream_t st);
+bool grow_dev(void** p, uint64_t* cap, uint64_t need);
+bool grow_pinned(void** p, uint64_t* cap, uint64_t need);
+uint64_t db_device_bytes(uint64_t n, uint32_t d, uint32_t z);
+}  // namespace tpir

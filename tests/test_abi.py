@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI boundary: the library builds for sm_103a, loads
+without a GPU, and exports every entry point include/talekpir.h declares; the
+Python binding declares a signature for each of them.  No compute call is made."""
+
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        names |= set(re.findall(r"\b(tpir_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("tpir_db_create", "tpir_write", "tpir_read_batch", "tpir_read_batch_async",
+                 "tpir_read_multi_async", "tpir_bloom_get", "tpir_serve_create",
+                 "tpir_serve_submit_read", "tpir_serve_poll", "tpir_serve_stats"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2001_08250_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2001_08250_gb300 import talekpir
+    bound = {name for name, _, _ in talekpir._SIGS}
+    assert _declared() <= bound, sorted(_declared() - bound)
+
+
+def test_library_built_for_sm103a_only():
+    from paper_2001_08250_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings_without_gpu():
+    from paper_2001_08250_gb300 import talekpir
+    assert talekpir.strerror(talekpir.EFULL).startswith("cuckoo table full")
+    assert "sm_103a" in talekpir.version()
+
+
+def test_invalid_arguments_rejected_before_any_device_work():
+    from paper_2001_08250_gb300 import talekpir
+    L = talekpir.lib()
+    assert L.tpir_db_create(0, 4, 1024) is None
+    assert L.tpir_last_error() == talekpir.EINVAL
+    assert L.tpir_db_create(16, 4, 1000) is None   # msg_bytes not a multiple of 16
+    assert L.tpir_db_create(16, 0, 1024) is None
+    assert L.tpir_read_batch(None, None, 1, None) == talekpir.EINVAL
+    assert L.tpir_read_multi_async(None, 200, None) == talekpir.EINVAL

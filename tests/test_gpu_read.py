@@ -1,0 +1,177 @@
+"""GPU parity of the PIR read kernels against the oracle, through the C ABI.
+
+Replies must be bit-exact.  Small and ragged shapes are compared element by
+element on every row; the paper-scale tables are compared on sampled rows and
+with a GF(2) Freivalds check of the whole batch, in the launch configuration
+the benchmark times."""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import check_rows, dev_out, freivalds, require_cuda, to_dev, to_host
+from paper_2001_08250_gb300 import synth, talekpir
+
+pytestmark = pytest.mark.gpu
+
+PLAIN, BATCHED = 1, 2
+
+
+def _db(n, d, z, T):
+    db = talekpir.DB(n, d, z)
+    db.load(T)
+    return db
+
+
+# n not a multiple of 32/64/stage rows, d = 1..8, msg 16..4096, B around
+# the tile edges, padding bits set (random_bits fills whole words)
+EDGE = [
+    (1, 1, 16, 1), (1, 4, 1024, 5), (63, 1, 16, 3), (64, 2, 48, 9), (65, 4, 16, 31),
+    (200, 8, 32, 33), (333, 2, 256, 64), (1000, 1, 4096, 17), (1024, 4, 1024, 257),
+    (4097, 2, 256, 40), (777, 3, 80, 12), (130, 8, 4096, 8), (2049, 1, 64, 100),
+]
+
+
+@pytest.mark.parametrize("n,d,z,B", EDGE)
+@pytest.mark.parametrize("kernel", [PLAIN, BATCHED])
+def test_edge_shapes_bit_exact(n, d, z, B, kernel):
+    require_cuda()
+    T = synth.table_bytes(n, d, z, seed=21, table=n * 7 + d)
+    R = synth.random_bits(B, n, seed=22, table=n)
+    exp = oracle.read_batch(T, n, d, z, R)
+    with _db(n, d, z, T) as db:
+        db.set_kernel(kernel)
+        got = db.read_batch(R)
+        assert np.array_equal(got, exp)
+        # the asynchronous device-buffer entry point gives the same replies
+        dR, dO = to_dev(R), dev_out(B, d * z)
+        db.read_batch_async(dR, B, dO)
+        assert np.array_equal(to_host(dO), exp)
+    assert talekpir.device_status() == talekpir.OK
+
+
+def test_empty_batch_and_zero_vector():
+    require_cuda()
+    n, d, z = 100, 2, 64
+    T = synth.table_bytes(n, d, z, seed=3)
+    with _db(n, d, z, T) as db:
+        assert db.read_batch(np.zeros((0, 2), dtype=np.uint64)).shape == (0, d * z)
+        for k in (PLAIN, BATCHED):
+            db.set_kernel(k)
+            assert not db.read_batch(np.zeros((6, 2), dtype=np.uint64)).any()
+            # one-hot rows return exactly their bucket
+            R = np.stack([synth.one_hot(n, t) for t in (0, 1, 63, 64, 99)])
+            assert np.array_equal(db.read_batch(R), T[[0, 1, 63, 64, 99]])
+
+
+def test_plain_pir_workload_cuckoo_filled_and_three_shares():
+    """n = 1024 buckets, d = 4, 1024-byte messages (4 MiB): filled to load 0.5
+    (2048 messages) through the device write path, then 64 reads, each split
+    into l = 3 XOR shares; every share's reply matches the oracle and the three
+    replies recombine to the target bucket."""
+    require_cuda()
+    n, d, z = 1024, 4, 1024
+    keys = synth.write_keys(2048, seed=0)
+    b1, b2 = synth.bucket_pairs(keys, n)
+    M = synth.messages(2048, z, seed=0)
+    oc = oracle.Cuckoo(n, d, z, 0, 500, seed=0)
+    for i in range(2048):
+        assert oc.insert(int(b1[i]), int(b2[i]), M[i])[0] == 0
+    T = oc.table()
+    with talekpir.DB(n, d, z) as db:
+        db.set_policy(0, 500, 0)
+        st, ev = db.write_batch(b1, b2, M)
+        assert (st == 0).all()
+        assert np.array_equal(db.dump(), T)
+        tg = synth.targets(64, n, seed=0)
+        S = synth.xor_shares(n, tg, 3, seed=0).reshape(192, -1)
+        for kernel in (PLAIN, BATCHED):
+            db.set_kernel(kernel)
+            got = db.read_batch(S)
+            assert np.array_equal(got, oracle.read_batch(T, n, d, z, S))
+            rec = got.reshape(64, 3, -1)
+            for i, t in enumerate(tg):
+                assert np.array_equal(rec[i, 0] ^ rec[i, 1] ^ rec[i, 2], T[t])
+
+
+@pytest.fixture(scope="module")
+def paper_scale():
+    n, d, z = 32768, 4, 1024
+    T = synth.table_bytes(n, d, z, seed=0)
+    return n, d, z, T
+
+
+@pytest.mark.parametrize("B", [1, 32, 256])
+def test_paper_scale_table_batches(paper_scale, B):
+    """n = 32768, d = 4, 1 KiB messages (128 MiB), Bernoulli(0.5) requests in
+    batches of B, through the device-buffer entry point the benchmark times."""
+    require_cuda()
+    n, d, z, T = paper_scale
+    R = synth.random_bits(B, n, seed=1, table=B)
+    with _db(n, d, z, T) as db:
+        dR, dO = to_dev(R), dev_out(B, d * z)
+        db.read_batch_async(dR, B, dO)
+        Out = to_host(dO)
+        check_rows(T, n, d, z, R, Out, sorted({0, B - 1, B // 2}))
+        freivalds(T, n, d, z, R, Out, trials=12, seed=B)
+        # forced kernels agree with the automatic choice
+        for k in (PLAIN, BATCHED):
+            db.set_kernel(k)
+            dO2 = dev_out(B, d * z)
+            db.read_batch_async(dR, B, dO2)
+            assert np.array_equal(to_host(dO2), Out)
+    assert talekpir.device_status() == talekpir.OK
+
+
+def test_paper_scale_three_share_recombination(paper_scale):
+    require_cuda()
+    n, d, z, T = paper_scale
+    tg = synth.targets(64, n, seed=5)
+    S = synth.xor_shares(n, tg, 3, seed=5).reshape(192, -1)
+    with _db(n, d, z, T) as db:
+        got = db.read_batch(S).reshape(64, 3, -1)
+    for i, t in enumerate(tg):
+        assert np.array_equal(got[i, 0] ^ got[i, 1] ^ got[i, 2], T[t])
+
+
+def test_multi_table_one_launch_bit_exact():
+    """Uneven tables (n, d, msg_bytes and B all differ) in one persistent launch."""
+    require_cuda()
+    shapes = [(1100, 2, 256, 16), (3000, 4, 1024, 40), (513, 8, 4096, 7), (2048, 2, 256, 300),
+              (97, 1, 16, 1), (4096, 4, 1024, 129), (700, 8, 256, 64), (64, 2, 4096, 33)]
+    dbs, jobs, exp = [], [], []
+    for i, (n, d, z, B) in enumerate(shapes):
+        T = synth.table_bytes(n, d, z, seed=30, table=i)
+        R = synth.random_bits(B, n, seed=31, table=i)
+        db = _db(n, d, z, T)
+        dbs.append(db)
+        dR, dO = to_dev(R), dev_out(B, d * z)
+        jobs.append((db, B, dR, dO))
+        exp.append(oracle.read_batch(T, n, d, z, R))
+    talekpir.read_multi_async(jobs)
+    for (db, B, dR, dO), e in zip(jobs, exp):
+        assert np.array_equal(to_host(dO), e)
+    for db in dbs:
+        db.close()
+    assert talekpir.device_status() == talekpir.OK
+
+
+def test_large_table_gf2_product_sampled():
+    """n = 2^20, d = 4, 1 KiB messages (4 GiB), B = 1024 packed request rows:
+    sampled rows plus a Freivalds check of the whole product, for the batched
+    kernel and, on a few rows, the plain kernel."""
+    require_cuda()
+    n, d, z, B = 1 << 20, 4, 1024, 1024
+    T = synth.table_bytes(n, d, z, seed=0, table=4)
+    R = synth.random_bits(B, n, seed=4)
+    with _db(n, d, z, T) as db:
+        dR, dO = to_dev(R), dev_out(B, d * z)
+        db.read_batch_async(dR, B, dO)
+        Out = to_host(dO)
+        check_rows(T, n, d, z, R, Out, [0, 511, 1023])
+        freivalds(T, n, d, z, R, Out, trials=8, seed=44)
+        db.set_kernel(PLAIN)
+        dO1 = dev_out(4, d * z)
+        db.read_batch_async(dR, 4, dO1)
+        assert np.array_equal(to_host(dO1), Out[:4])
+    assert talekpir.device_status() == talekpir.OK
