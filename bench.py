@@ -158,10 +158,16 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--legs", default="head,plain,b32,e2e,serve,cpu",
+                    help="comma list of: head (B=256, timed headline), plain (B=1), b32, "
+                         "e2e (host buffers), serve, cpu (oracle baseline)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    args.legs = set(args.legs.split(","))
+    if args.no_serve:
+        args.legs.discard("serve")
 
     if args.impl == "reference":
         run_reference(args)
@@ -252,7 +258,10 @@ def main() -> None:
 
     # ---- headline: batch width 256, batched kernel
     clocks = ClockSampler(local)
-    ms, durs, ck = timed(B_HEAD, args.steps, args.warmup, with_launch_events=True, clocks=clocks)
+    if "head" in args.legs:
+        ms, durs, ck = timed(B_HEAD, args.steps, args.warmup, with_launch_events=True, clocks=clocks)
+    else:
+        ms, durs, ck = float("nan"), [float("nan")], None
     ms = max_over_ranks(ms)
     value = USERS * world / (ms * 1e-3)
     launch_ms = statistics.mean(durs)
@@ -263,12 +272,17 @@ def main() -> None:
 
     # ---- legs: plain (B=1) and B=32
     legs = {}
-    for B, steps in ((1, max(2, args.steps // 4)), (32, max(3, args.steps // 2))):
-        bms, bd, _ = timed(B, steps, 1, with_launch_events=(B == 1))
+    for B, steps, name in ((1, max(2, args.steps // 4), "plain"), (32, max(3, args.steps // 2), "b32")):
+        if name not in args.legs:
+            legs[str(B)] = {"reads_per_s": float("nan"), "scan_gbs": float("nan")}
+            continue
+        bms, bd, _ = timed(B, steps, 1)
         bms = max_over_ranks(bms)
         legs[str(B)] = {"reads_per_s": USERS * world / (bms * 1e-3), "ms_per_step": bms}
         if B == 1:
-            pl_ms = statistics.mean(bd)
+            # average duration of one read = the timed region / reads (events
+            # between launches would break their programmatic overlap)
+            pl_ms = bms / USERS
             legs["1"]["scan_gbs"] = algo_bytes_per_read / (pl_ms * 1e-3) / 1e9
             legs["1"]["launch_ms"] = pl_ms
         else:
@@ -288,25 +302,27 @@ def main() -> None:
             rc = L.tpir_read_batch(dbs[i % COPIES].h, hR[b0:b0 + nb].ctypes.data, nb,
                                    hO[b0:b0 + nb].ctypes.data)
             assert rc == 0, rc
-    for _ in range(args.warmup):
-        e2e_step()
-    e2e_steps = max(2, args.steps // 2)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
-    e2e = {"value": USERS * world / e2e_s, "unit": "reads/s",
-           "h2d_bytes_per_step": int(USERS * words * 8), "d2h_bytes_per_step": int(USERS * row)}
+    e2e = None
+    if "e2e" in args.legs:
+        for _ in range(args.warmup):
+            e2e_step()
+        e2e_steps = max(2, args.steps // 2)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+        e2e = {"value": USERS * world / e2e_s, "unit": "reads/s",
+               "h2d_bytes_per_step": int(USERS * words * 8), "d2h_bytes_per_step": int(USERS * row)}
 
     # ---- short serve run (continuous batching), rank 0 only
     serve = None
-    if not args.no_serve and rank == 0:
+    if "serve" in args.legs and rank == 0:
         serve = serve_leg(talekpir, synth, args.serve_rate, args.serve_seconds)
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
     cpu = None
-    if rank == 0:
+    if rank == 0 and "cpu" in args.legs:
         import oracle
         oracle.build()
         sample = 8

@@ -120,9 +120,11 @@ tpir_status tpir_read_batch(tpir_db *db, const uint64_t *req_bits, uint32_t B, v
 tpir_status tpir_read_batch_async(tpir_db *db, const uint64_t *d_req_bits, uint32_t B,
                                   void *d_out, void *stream);
 
-/* Force a kernel choice for tests and benchmarks: 0 = automatic (the tuned
- * plan), 1 = plain streaming kernel (B <= 4 per launch, larger B is split into
- * launches), 2 = batched register-tiled kernel. */
+/* Force a kernel choice for tests and benchmarks: 0 = automatic (plain for
+ * B <= 4, batched otherwise), 1 = plain streaming kernel (B <= 4 per launch,
+ * larger B is split into launches; TMA-staged where the row width allows),
+ * 2 = batched register-tiled kernel, 3 = plain kernel with register
+ * streaming only (the path used for row widths the TMA-staged one skips). */
 tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
 
 /* Many tables in ONE persistent launch (the uneven-batching workload): job i

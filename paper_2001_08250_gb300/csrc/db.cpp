@@ -140,7 +140,7 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
   int kernel = db->forced_kernel;
   if (kernel == 0) kernel = (B <= kPlainMaxB) ? 1 : 2;
   cudaError_t e = cudaSuccess;
-  if (kernel == 1) {
+  if (kernel == 1 || kernel == 3) {
     const uint32_t* T = reinterpret_cast<const uint32_t*>(db->d_table);
     for (uint32_t b0 = 0; b0 < B && e == cudaSuccess; b0 += kPlainMaxB) {
       const uint32_t nb = std::min(kPlainMaxB, B - b0);
@@ -148,7 +148,7 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
                        db->words64, nb,
                        reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_out) +
                                                    static_cast<uint64_t>(b0) * db->row_bytes),
-                       st, 0);
+                       st, kernel == 3 ? -1 : 0);
     }
   } else {
     ScanLaunch L;
@@ -397,7 +397,7 @@ tpir_status tpir_db_set_policy(tpir_db* db, uint64_t capacity, uint32_t max_evic
 }
 
 tpir_status tpir_db_set_kernel(tpir_db* db, int kernel) {
-  if (!db || kernel < 0 || kernel > 2) return TPIR_EINVAL;
+  if (!db || kernel < 0 || kernel > 3) return TPIR_EINVAL;
   db->forced_kernel = kernel;
   return TPIR_OK;
 }

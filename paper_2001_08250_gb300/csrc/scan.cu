@@ -16,6 +16,8 @@
 //                       one LOP3 (acc ^= mask & word) per request-word pair.
 //                       Items are (job, B-tile, W-tile, k-chunk), so the same
 //                       launch serves one table or many uneven tables.
+#include <algorithm>
+
 #include "tpir_internal.h"
 
 namespace tpir {
@@ -83,6 +85,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return true;
 }
 
+// Like mbar_wait, with a short sleep between polls: for waiters that run
+// ahead of the pipeline and should leave issue slots to the compute warps.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity,
+                                                  volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      atomicExch(&g_status, (int)TPIR_ETIMEDOUT);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// Named barrier of the producer warpgroup (id 1; id 0 is __syncthreads).
+__device__ __forceinline__ void producer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kProducerThreads) : "memory");
+}
+
 // 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
                                          uint64_t* bar) {
@@ -110,12 +135,23 @@ __device__ __forceinline__ uint32_t bit_mask(uint64_t w, uint32_t pos) {
   return 0u - static_cast<uint32_t>((w >> pos) & 1u);
 }
 
+// Programmatic dependent launch: let the next kernel of the stream start its
+// launch now / wait until the previous kernel of the stream has completed and
+// its memory is visible.  Both are no-ops without a programmatic dependency.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Plain streaming kernel
 // ---------------------------------------------------------------------------
-// grid.y = column slices of <= 256 uint4 (4 KiB) of a row, grid.x = bucket
-// ranges of rows_per_cta.  A slice narrower than 256 uint4 is covered by
-// 256/Us rows at once; those partials are folded in shared memory.
+// grid.y = column slices of <= kPlainSlice uint4 (512 B) of a row, grid.x =
+// bucket ranges of rows_per_cta.  The 256 threads cover 256/Us rows of the
+// slice at once (one warp per 512 B row segment); their partials are folded in
+// shared memory, so each output word receives one red.xor per bucket range.
+constexpr uint32_t kPlainSlice = 32;  // uint4 per column slice
+
 template <int NB, int UNR>
 __global__ void __launch_bounds__(256) plain_scan_kernel(const uint4* __restrict__ T, uint64_t n,
                                                          uint32_t U,
@@ -124,8 +160,9 @@ __global__ void __launch_bounds__(256) plain_scan_kernel(const uint4* __restrict
                                                          uint4* __restrict__ out,
                                                          uint64_t rows_per_cta) {
   __shared__ uint4 fold[NB * 256];
-  const uint32_t c0 = blockIdx.y * 256u;
-  const uint32_t Us = min(256u, U - c0);
+  pdl_launch_dependents();
+  const uint32_t c0 = blockIdx.y * kPlainSlice;
+  const uint32_t Us = min(kPlainSlice, U - c0);
   const uint32_t rpi = 256u / Us;
   const uint32_t t = threadIdx.x;
   const bool active = t < rpi * Us;
@@ -140,15 +177,20 @@ __global__ void __launch_bounds__(256) plain_scan_kernel(const uint4* __restrict
 
   if (active && k0 < k1) {
     const uint4* base = T + c0 + cl;
-    uint64_t k = k0 + roff;
     const uint64_t step = rpi;
-    for (; k + (UNR - 1) * step < k1; k += UNR * step) {
+    // UNR rows in flight per thread; rows past the range are neither loaded
+    // nor combined (they belong to another CTA or lie beyond the table)
+    for (uint64_t k = k0 + roff; k < k1; k += UNR * step) {
       uint4 v[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) v[u] = ld_stream(base + (k + u * step) * U);
 #pragma unroll
       for (int u = 0; u < UNR; ++u) {
         const uint64_t kk = k + u * step;
+        v[u] = kk < k1 ? ld_stream(base + kk * U) : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const uint64_t kk = k + u * step;
+        if (kk >= k1) break;
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
           if (b < (int)B) {
@@ -158,19 +200,6 @@ __global__ void __launch_bounds__(256) plain_scan_kernel(const uint4* __restrict
             acc[b].z ^= v[u].z & m;
             acc[b].w ^= v[u].w & m;
           }
-        }
-      }
-    }
-    for (; k < k1; k += step) {
-      const uint4 v = ld_stream(base + k * U);
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        if (b < (int)B) {
-          const uint32_t m = bit_mask(__ldg(R + b * (uint64_t)words64 + (k >> 6)), k & 63);
-          acc[b].x ^= v.x & m;
-          acc[b].y ^= v.y & m;
-          acc[b].z ^= v.z & m;
-          acc[b].w ^= v.w & m;
         }
       }
     }
@@ -194,6 +223,8 @@ __global__ void __launch_bounds__(256) plain_scan_kernel(const uint4* __restrict
       }
     }
   }
+  // the reply was zeroed by the previous kernel of the stream
+  pdl_wait();
   if (t < Us && k0 < k1) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -201,6 +232,160 @@ __global__ void __launch_bounds__(256) plain_scan_kernel(const uint4* __restrict
         uint32_t* o = reinterpret_cast<uint32_t*>(out + static_cast<uint64_t>(b) * U + c0 + t);
         red_xor64(o, acc[b].x, acc[b].y);
         red_xor64(o + 2, acc[b].z, acc[b].w);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plain TMA streaming kernel
+// ---------------------------------------------------------------------------
+// One CTA per SM streams a contiguous bucket range through a ring of
+// kPlainStages shared-memory stages, each filled by ONE 1-D bulk copy of whole
+// rows (up to kPlainStageBytes), so ~192 KiB per SM are in flight whatever the
+// register pressure.  Eight consumer warps XOR the staged rows: with U <= 256
+// uint4 per row (U dividing 256), thread t owns column t % U of every
+// (256/U)-th row; with U = 256*CPT it owns columns t, t+256, ... of every row.
+// Partials of threads sharing a column are folded in shared memory and the
+// CTA's reply is XOR-reduced into the zeroed output with red.xor.
+constexpr int kPlainStages = 6;
+constexpr int kPlainStageBytes = 32 * 1024;
+constexpr int kPlainThreads = 32 * 9;  // 8 consumer warps + 1 producer warp
+constexpr int kPlainTmaSmem = kPlainStages * kPlainStageBytes + 128;
+
+template <int NB, int CPT>
+__global__ void __launch_bounds__(kPlainThreads, 1)
+    plain_tma_kernel(const uint4* __restrict__ T, uint64_t n, uint32_t U,
+                     const uint64_t* __restrict__ R, uint32_t words64, uint32_t B,
+                     uint4* __restrict__ out, uint64_t rows_per_cta) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + kPlainStages;
+  uint4* stages = reinterpret_cast<uint4*>(smem_raw + 128);
+  __shared__ int s_abort;
+  constexpr int NC = CPT > 0 ? CPT : 1;  // accumulators per request
+
+  pdl_launch_dependents();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t k0 = static_cast<uint64_t>(blockIdx.x) * rows_per_cta;
+  const uint64_t k1 = min(n, k0 + rows_per_cta);
+  const uint32_t stage_rows = max(1u, static_cast<uint32_t>(kPlainStageBytes / (U * 16u)));
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPlainStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 8);
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  volatile int* abort_flag = &s_abort;
+
+  if (warp == 8) {
+    // ---- producer: one bulk copy per stage
+    uint32_t iter = 0;
+    if (lane == 0) {
+      for (uint64_t ks = k0; ks < k1; ks += stage_rows, ++iter) {
+        const uint32_t s = iter % kPlainStages, ph = (iter / kPlainStages) & 1u;
+        if (!mbar_wait_backoff(&empty[s], ph ^ 1u, abort_flag)) break;
+        const uint32_t rows = static_cast<uint32_t>(k1 - ks < stage_rows ? k1 - ks : stage_rows);
+        const uint32_t bytes = rows * U * 16u;
+        mbar_expect_tx(&full[s], bytes);
+        bulk_g2s(stages + static_cast<uint64_t>(s) * (kPlainStageBytes / 16), T + ks * U, bytes,
+                 &full[s]);
+        mbar_arrive(&full[s]);
+      }
+      if (*abort_flag) {
+        const uint32_t first = iter > kPlainStages ? iter - kPlainStages : 0;
+        for (uint32_t x = first; x < iter; ++x) {
+          const uint64_t t0 = globaltimer();
+          while (!mbar_try_wait(&full[x % kPlainStages], (x / kPlainStages) & 1u) &&
+                 globaltimer() - t0 < kWaitLimitNs) {
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  // ---- consumers
+  const uint32_t t = threadIdx.x;  // 0..255
+  const uint32_t rpi = CPT > 0 ? 1u : 256u / U;
+  const uint32_t roff = CPT > 0 ? 0u : t / U;
+  const uint32_t col = CPT > 0 ? t : t % U;
+  uint4 acc[NB][NC];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[b][c] = make_uint4(0u, 0u, 0u, 0u);
+
+  uint32_t iter = 0;
+  bool ok = true;
+  for (uint64_t ks = k0; ks < k1; ks += stage_rows, ++iter) {
+    const uint32_t s = iter % kPlainStages, ph = (iter / kPlainStages) & 1u;
+    if (!mbar_wait(&full[s], ph, abort_flag)) {
+      ok = false;
+      break;
+    }
+    const uint4* st = stages + static_cast<uint64_t>(s) * (kPlainStageBytes / 16);
+    const uint32_t rows = static_cast<uint32_t>(k1 - ks < stage_rows ? k1 - ks : stage_rows);
+    for (uint32_t r = roff; r < rows; r += rpi) {
+      const uint64_t k = ks + r;
+      uint32_t m[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        m[b] = b < (int)B ? bit_mask(__ldg(R + b * (uint64_t)words64 + (k >> 6)), k & 63) : 0u;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const uint4 v = st[r * U + col + c * 256u];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          acc[b][c].x ^= v.x & m[b];
+          acc[b][c].y ^= v.y & m[b];
+          acc[b][c].z ^= v.z & m[b];
+          acc[b][c].w ^= v.w & m[b];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  // (after a give-up every consumer still passes the fold barriers below, so
+  // none waits for a peer that left; only the reduction is skipped)
+
+  // fold the partials of threads that share a column (U < 256), then reduce
+  if (CPT == 0 && rpi > 1) {
+    // the ring is idle now: reuse stage 0's first 256*NB uint4 as fold space
+    asm volatile("bar.sync 2, 256;" ::: "memory");
+    uint4* fold = stages;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) fold[b * 256 + t] = acc[b][0];
+    asm volatile("bar.sync 2, 256;" ::: "memory");
+    if (t < U) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t r = 0; r < rpi; ++r) {
+          const uint4 p = fold[b * 256 + r * U + t];
+          x.x ^= p.x;
+          x.y ^= p.y;
+          x.z ^= p.z;
+          x.w ^= p.w;
+        }
+        acc[b][0] = x;
+      }
+    }
+  }
+  pdl_wait();
+  if (ok && !*abort_flag && k0 < k1 && (CPT > 0 || t < U)) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (b >= (int)B) continue;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        uint32_t* o = reinterpret_cast<uint32_t*>(out + static_cast<uint64_t>(b) * U + col + c * 256u);
+        red_xor64(o, acc[b][c].x, acc[b][c].y);
+        red_xor64(o + 2, acc[b][c].z, acc[b][c].w);
       }
     }
   }
@@ -240,6 +425,136 @@ __device__ __forceinline__ Item decode_item(const ScanLaunch& L, uint32_t item) 
   return it;
 }
 
+__device__ __forceinline__ uint4 lds4(const uint32_t* p) {
+  return *reinterpret_cast<const uint4*>(p);
+}
+
+__device__ __forceinline__ void xor_row(uint32_t (&acc)[kMR][kNW], const uint4& m0, const uint4& m1,
+                                        const uint4& t0, const uint4& t1, const uint4& t2,
+                                        const uint4& t3) {
+  const uint32_t m[kMR] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+  const uint32_t w[kNW] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w,
+                           t2.x, t2.y, t2.z, t2.w, t3.x, t3.y, t3.z, t3.w};
+#pragma unroll
+  for (int i = 0; i < kMR; ++i)
+#pragma unroll
+    for (int q = 0; q < kNW; ++q) acc[i][q] ^= m[i] & w[q];
+}
+
+__device__ __forceinline__ uint4 lds4a(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+// One consumer warp's `nr` rows of a stage (rows first, first + wk, ...),
+// addressed by 32-bit shared-memory byte offsets; a thread's four 16-byte
+// table segments are SEG bytes apart.  Two operand sets (A, B) alternate: the
+// masks and table words of the next row are loaded while the current row's
+// 128 LOP3s run, and no register is copied between iterations.  (One code
+// path for every lane layout: per-layout copies of this loop overflow the
+// consumer register budget.)
+__device__ __forceinline__ void consume_rows(uint32_t (&acc)[kMR][kNW], uint32_t ma, uint32_t ta,
+                                             uint32_t nr, uint32_t mstep, uint32_t tstep,
+                                             uint32_t SEG) {
+  if (nr == 0) return;
+  uint4 am0 = lds4a(ma), am1 = lds4a(ma + 16);
+  uint4 at0 = lds4a(ta), at1 = lds4a(ta + SEG), at2 = lds4a(ta + 2 * SEG), at3 = lds4a(ta + 3 * SEG);
+  uint4 bm0, bm1, bt0, bt1, bt2, bt3;
+  for (;;) {
+    if (nr > 1) {
+      ma += mstep;
+      ta += tstep;
+      bm0 = lds4a(ma);
+      bm1 = lds4a(ma + 16);
+      bt0 = lds4a(ta);
+      bt1 = lds4a(ta + SEG);
+      bt2 = lds4a(ta + 2 * SEG);
+      bt3 = lds4a(ta + 3 * SEG);
+    }
+    xor_row(acc, am0, am1, at0, at1, at2, at3);
+    if (--nr == 0) break;
+    if (nr > 1) {
+      ma += mstep;
+      ta += tstep;
+      am0 = lds4a(ma);
+      am1 = lds4a(ma + 16);
+      at0 = lds4a(ta);
+      at1 = lds4a(ta + SEG);
+      at2 = lds4a(ta + 2 * SEG);
+      at3 = lds4a(ta + 3 * SEG);
+    }
+    xor_row(acc, bm0, bm1, bt0, bt1, bt2, bt3);
+    if (--nr == 0) break;
+  }
+}
+
+// One consumer warp's share of one item: wait for each stage, XOR its rows,
+// release the stage, then store (single k-chunk) or XOR-reduce (split) the
+// 8-request x 16-word register tile.  Returns false if a wait gave up.
+__device__ __forceinline__ bool consume_item(const ScanJob& J, const Item& it, uint32_t cw,
+                                             uint32_t lane, uint64_t* full, uint64_t* empty,
+                                             uint8_t* stages, volatile int* abort_flag,
+                                             uint32_t& iter) {
+  const uint32_t LW_LOG2 = J.shape.lw_log2;
+  const uint32_t LW = 1u << LW_LOG2;
+  const uint32_t ww = J.shape.ww, wbw = J.shape.wb * ww, wk = J.shape.wk;
+  const uint32_t bt_ = J.shape.bt(), wt_ = J.shape.wt(), sr = J.shape.srows();
+  const uint32_t wk_idx = cw / wbw, rem = cw % wbw;
+  const uint32_t wb_idx = rem / ww, ww_idx = rem % ww;
+  const uint32_t lwi = lane & (LW - 1), lbi = lane >> LW_LOG2;
+  const uint32_t rq0 = (wb_idx * (32u >> LW_LOG2) + lbi) * kMR;
+  const uint32_t wbase = ww_idx * (LW * kNW) + lwi * 4u;
+
+  uint32_t acc[kMR][kNW];
+#pragma unroll
+  for (int i = 0; i < kMR; ++i)
+#pragma unroll
+    for (int q = 0; q < kNW; ++q) acc[i][q] = 0u;
+
+  const uint32_t moff = (wk_idx * bt_ + rq0) * 4u, toff = (wk_idx * wt_ + wbase) * 4u;
+  const uint32_t mstep = wk * bt_ * 4u, tstep = wk * wt_ * 4u;
+  const uint32_t stage0 = smem_u32(stages);
+  for (uint64_t ks = it.k0; ks < it.k1; ks += sr, ++iter) {
+    const uint32_t s = iter % kStages;
+    const uint32_t ph = (iter / kStages) & 1u;
+    if (!mbar_wait(&full[s], ph, abort_flag)) return false;
+    const uint32_t rows = static_cast<uint32_t>(it.k1 - ks < sr ? it.k1 - ks : sr);
+    const uint32_t nr = rows > wk_idx ? (rows - wk_idx + wk - 1) / wk : 0u;
+    const uint32_t tbase = stage0 + s * kStageBytes;
+    consume_rows(acc, tbase + sr * wt_ * 4u + moff, tbase + toff, nr, mstep, tstep, LW * 16u);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+
+  // outputs are zeroed / released by the previous kernel of the stream
+  pdl_wait();
+  const bool split = J.split != 0;
+  const uint32_t b0 = it.bt * bt_ + rq0;
+  const uint32_t w0 = it.wt * wt_ + wbase;
+#pragma unroll
+  for (int i = 0; i < kMR; ++i) {
+    const uint32_t b = b0 + i;
+    if (b >= J.B) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t wd = w0 + j * LW * 4u;
+      if (wd >= J.Wd) continue;
+      uint32_t* o = J.out + static_cast<uint64_t>(b) * J.Wd + wd;
+      if (split) {
+        red_xor64(o, acc[i][4 * j], acc[i][4 * j + 1]);
+        red_xor64(o + 2, acc[i][4 * j + 2], acc[i][4 * j + 3]);
+      } else {
+        *reinterpret_cast<uint4*>(o) =
+            make_uint4(acc[i][4 * j], acc[i][4 * j + 1], acc[i][4 * j + 2], acc[i][4 * j + 3]);
+      }
+    }
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kScanThreads, 1)
     batched_scan_kernel(const __grid_constant__ ScanLaunch L) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -247,12 +562,14 @@ __global__ void __launch_bounds__(kScanThreads, 1)
   uint64_t* empty = full + kStages;
   uint8_t* stages = smem_raw + 256;
   __shared__ int s_abort;
+  __shared__ volatile int s_go[2];
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  pdl_launch_dependents();
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 32);
+      mbar_init(&full[s], kProducerThreads);
       mbar_init(&empty[s], kConsumerWarps);
     }
     s_abort = 0;
@@ -263,8 +580,11 @@ __global__ void __launch_bounds__(kScanThreads, 1)
 
   uint32_t iter = 0;  // pipeline stage counter, identical in producer and consumers
 
-  if (warp == kConsumerWarps) {
-    // ---------------- producer warp ----------------
+  if (threadIdx.x < kProducerThreads) {
+    // ---------------- producer warpgroup ----------------
+    // warp 0 issues the bulk copies; all 128 threads expand request bits
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
+    const uint32_t ptid = threadIdx.x;
     bool ok = true;
     for (uint32_t item = blockIdx.x; ok && item < L.total_items; item += gridDim.x) {
       const Item it = decode_item(L, item);
@@ -276,21 +596,29 @@ __global__ void __launch_bounds__(kScanThreads, 1)
       for (uint64_t ks = it.k0; ks < it.k1; ks += sr, ++iter) {
         const uint32_t s = iter % kStages;
         const uint32_t ph = (iter / kStages) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+        // one thread polls the slot's release and publishes the outcome; the
+        // warpgroup waits on a hardware barrier instead of spinning.  The
+        // outcome slot alternates with the stage parity so that a fast thread
+        // 0 cannot overwrite it before the others have read it.
+        if (ptid == 0) s_go[iter & 1u] = mbar_wait_backoff(&empty[s], ph ^ 1u, abort_flag) ? 1 : 0;
+        producer_sync();
+        if (!s_go[iter & 1u]) {
           ok = false;
           break;
         }
         uint32_t* tsm = reinterpret_cast<uint32_t*>(stages + s * kStageBytes);
         uint32_t* msm = tsm + sr * wt_;
         const uint32_t rows = static_cast<uint32_t>(it.k1 - ks < sr ? it.k1 - ks : sr);
-        if (lane == 0) mbar_expect_tx(&full[s], rows * wcount * 4u);
-        __syncwarp();
-        for (uint32_t r = lane; r < rows; r += 32)
-          bulk_g2s(tsm + r * wt_, J.T + (ks + r) * J.Wd + w0, wcount * 4u, &full[s]);
+        if (warp == 0) {
+          if (lane == 0) mbar_expect_tx(&full[s], rows * wcount * 4u);
+          __syncwarp();
+          for (uint32_t r = lane; r < rows; r += 32)
+            bulk_g2s(tsm + r * wt_, J.T + (ks + r) * J.Wd + w0, wcount * 4u, &full[s]);
+        }
         // request bits -> 32-bit masks, zero for rows past the chunk and for
         // request slots past B
         const uint32_t sh = static_cast<uint32_t>(ks & 63);
-        for (uint32_t b = lane; b < bt_; b += 32) {
+        for (uint32_t b = ptid; b < bt_; b += kProducerThreads) {
           uint64_t wbits = 0;
           if (b0 + b < J.B) wbits = __ldg(J.R + static_cast<uint64_t>(b0 + b) * J.words64 + (ks >> 6));
           wbits >>= sh;
@@ -300,7 +628,7 @@ __global__ void __launch_bounds__(kScanThreads, 1)
         mbar_arrive(&full[s]);
       }
     }
-    if (*abort_flag && lane == 0) {
+    if (*abort_flag && ptid == 0) {
       // give the copies already issued a bounded chance to land before exit
       const uint32_t first = iter > kStages ? iter - kStages : 0;
       for (uint32_t x = first; x < iter; ++x) {
@@ -313,88 +641,33 @@ __global__ void __launch_bounds__(kScanThreads, 1)
     return;
   }
 
-  // ---------------- consumer warps ----------------
-  const int cw = warp;
+  // ---------------- consumer warpgroups ----------------
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
+  const uint32_t cw = static_cast<uint32_t>(warp - kProducerThreads / 32);
   for (uint32_t item = blockIdx.x; item < L.total_items; item += gridDim.x) {
     const Item it = decode_item(L, item);
     const ScanJob& J = L.jobs[it.job];
-    const uint32_t lw_log2 = J.shape.lw_log2;
-    const uint32_t lw = 1u << lw_log2;
-    const uint32_t ww = J.shape.ww, wbw = J.shape.wb * ww, wk = J.shape.wk;
-    const uint32_t bt_ = J.shape.bt(), wt_ = J.shape.wt(), sr = J.shape.srows();
-    const uint32_t wk_idx = cw / wbw, rem = cw % wbw;
-    const uint32_t wb_idx = rem / ww, ww_idx = rem % ww;
-    const uint32_t lwi = lane & (lw - 1), lbi = lane >> lw_log2;
-    const uint32_t rq0 = (wb_idx * (32u >> lw_log2) + lbi) * kMR;
-    const uint32_t wbase = ww_idx * (lw * kNW) + lwi * 4u;
-    const uint32_t seg = lw * 4u;
-
-    uint32_t acc[kMR][kNW];
-#pragma unroll
-    for (int i = 0; i < kMR; ++i)
-#pragma unroll
-      for (int q = 0; q < kNW; ++q) acc[i][q] = 0u;
-
-    bool ok = true;
-    for (uint64_t ks = it.k0; ks < it.k1; ks += sr, ++iter) {
-      const uint32_t s = iter % kStages;
-      const uint32_t ph = (iter / kStages) & 1u;
-      if (!mbar_wait(&full[s], ph, abort_flag)) {
-        ok = false;
-        break;
-      }
-      const uint32_t* tsm = reinterpret_cast<const uint32_t*>(stages + s * kStageBytes);
-      const uint32_t* msm = tsm + sr * wt_;
-      const uint32_t rows = static_cast<uint32_t>(it.k1 - ks < sr ? it.k1 - ks : sr);
-      for (uint32_t r = wk_idx; r < rows; r += wk) {
-        const uint4 m0 = *reinterpret_cast<const uint4*>(msm + r * bt_ + rq0);
-        const uint4 m1 = *reinterpret_cast<const uint4*>(msm + r * bt_ + rq0 + 4);
-        uint4 tv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          tv[j] = *reinterpret_cast<const uint4*>(tsm + r * wt_ + wbase + j * seg);
-        const uint32_t m[kMR] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-        const uint32_t w[kNW] = {tv[0].x, tv[0].y, tv[0].z, tv[0].w, tv[1].x, tv[1].y,
-                                 tv[1].z, tv[1].w, tv[2].x, tv[2].y, tv[2].z, tv[2].w,
-                                 tv[3].x, tv[3].y, tv[3].z, tv[3].w};
-#pragma unroll
-        for (int i = 0; i < kMR; ++i)
-#pragma unroll
-          for (int q = 0; q < kNW; ++q) acc[i][q] ^= m[i] & w[q];
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-    }
-    if (!ok) return;
-
-    // epilogue: store (single k-chunk) or XOR-reduce (split over k-chunks)
-    const bool split = J.split != 0;
-    const uint32_t b0 = it.bt * bt_ + rq0;
-    const uint32_t w0 = it.wt * wt_ + wbase;
-#pragma unroll
-    for (int i = 0; i < kMR; ++i) {
-      const uint32_t b = b0 + i;
-      if (b >= J.B) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t wd = w0 + j * seg;
-        if (wd >= J.Wd) continue;
-        uint32_t* o = J.out + static_cast<uint64_t>(b) * J.Wd + wd;
-        if (split) {
-          red_xor64(o, acc[i][4 * j], acc[i][4 * j + 1]);
-          red_xor64(o + 2, acc[i][4 * j + 2], acc[i][4 * j + 3]);
-        } else {
-          *reinterpret_cast<uint4*>(o) =
-              make_uint4(acc[i][4 * j], acc[i][4 * j + 1], acc[i][4 * j + 2], acc[i][4 * j + 3]);
-        }
-      }
-    }
+    if (!consume_item(J, it, cw, lane, full, empty, stages, abort_flag, iter)) return;
   }
+}
+
+// Zeroes a reply buffer before a scan XOR-reduces into it.  It lets the scan
+// launch at once (the scan only waits for it before its reduction) but waits
+// itself for the previous kernel, which may still be reducing into a buffer
+// the caller reuses.
+__global__ void zero_u4_kernel(uint4* __restrict__ out, uint64_t n4) {
+  pdl_launch_dependents();
+  pdl_wait();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // Zeroes the outputs of the jobs that are split over k-chunks (their CTAs
 // XOR-reduce into the output).  grid.y = job.
 __global__ void zero_outputs_kernel(const __grid_constant__ ScanLaunch L) {
+  pdl_launch_dependents();
+  pdl_wait();
   const ScanJob& J = L.jobs[blockIdx.y];
   if (!J.split) return;
   const uint64_t n4 = static_cast<uint64_t>(J.B) * J.Wd / 4;
@@ -422,14 +695,34 @@ int device_sm_count() {
   return cached[dev];
 }
 
-int plain_ctas_per_sm() {
+template <int NB>
+static int plain_occupancy() {
   static int cached = 0;
   if (!cached) {
     int v = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, plain_scan_kernel<4, 8>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, plain_scan_kernel<NB, 8>, 256, 0);
     cached = v > 0 ? v : 1;
   }
   return cached;
+}
+
+int plain_ctas_per_sm() { return plain_occupancy<1>(); }
+
+// Launch with programmatic stream serialisation (PDL) allowed.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 int batched_ctas_per_sm() {
@@ -498,48 +791,99 @@ bool finalize_job(ScanJob& j) {
 cudaError_t launch_batched(const ScanLaunch& L, int grid, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(batched_scan_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSmem);
+    // the setmaxnreg split is only safe with the register count it was sized for
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, batched_scan_kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs != kScanLaunchRegs) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(batched_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kScanSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   if (L.total_items == 0) return cudaSuccess;
-  batched_scan_kernel<<<grid, kScanThreads, kScanSmem, st>>>(L);
-  return cudaGetLastError();
+  return launch_pdl(batched_scan_kernel, dim3(grid), dim3(kScanThreads), kScanSmem, st, L);
 }
 
 cudaError_t launch_zero_outputs(const ScanLaunch& L, cudaStream_t st) {
   bool any = false;
   for (uint32_t i = 0; i < L.njobs; ++i) any |= L.jobs[i].split != 0;
   if (!any) return cudaSuccess;
-  dim3 grid(64, L.njobs);
-  zero_outputs_kernel<<<grid, 256, 0, st>>>(L);
-  return cudaGetLastError();
+  return launch_pdl(zero_outputs_kernel, dim3(64, L.njobs), dim3(256), 0, st, L);
+}
+
+template <int NB, int CPT>
+static cudaError_t launch_plain_tma_t(const uint4* T4, uint64_t n, uint32_t U, const uint64_t* R,
+                                      uint32_t words64, uint32_t B, uint4* o4, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(plain_tma_kernel<NB, CPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPlainTmaSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  uint64_t ctas = std::min<uint64_t>(device_sm_count(), n);
+  const uint64_t rows_per_cta = (n + ctas - 1) / ctas;
+  ctas = (n + rows_per_cta - 1) / rows_per_cta;
+  return launch_pdl(plain_tma_kernel<NB, CPT>, dim3(static_cast<uint32_t>(ctas)),
+                    dim3(kPlainThreads), kPlainTmaSmem, st, T4, n, U, R, words64, B, o4,
+                    rows_per_cta);
+}
+
+template <int NB, int CMAX>
+static cudaError_t launch_plain_tma(const uint4* T4, uint64_t n, uint32_t U, const uint64_t* R,
+                                    uint32_t words64, uint32_t B, uint4* o4, cudaStream_t st) {
+  if (U <= 256) return launch_plain_tma_t<NB, 0>(T4, n, U, R, words64, B, o4, st);
+  switch (U / 256) {
+    case 1: return launch_plain_tma_t<NB, 1>(T4, n, U, R, words64, B, o4, st);
+    case 2: return launch_plain_tma_t<NB, 2>(T4, n, U, R, words64, B, o4, st);
+    case 4: return launch_plain_tma_t<NB, 4>(T4, n, U, R, words64, B, o4, st);
+    default: return launch_plain_tma_t<NB, CMAX>(T4, n, U, R, words64, B, o4, st);
+  }
+}
+
+// Rows the TMA kernel handles: U dividing 256, or U = 256 * {1,2,4,8}; the
+// 4-request variant stops at 4 column groups (its accumulators must stay in
+// registers).
+static bool plain_tma_ok(uint32_t U, int nb) {
+  if (U <= 256) return (256 % U) == 0;
+  const uint32_t c = U / 256;
+  const uint32_t cmax = nb == 4 ? 4 : 8;
+  return (U % 256) == 0 && (c == 1 || c == 2 || c == 4 || c == 8) && c <= cmax;
 }
 
 cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
                          uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st, int ctas) {
   if (B == 0) return cudaSuccess;
   const uint32_t U = Wd / 4;
-  cudaError_t e = cudaMemsetAsync(out, 0, static_cast<size_t>(B) * Wd * 4, st);
+  uint4* o4 = reinterpret_cast<uint4*>(out);
+  const uint64_t n4 = static_cast<uint64_t>(B) * U;
+  cudaError_t e = launch_pdl(zero_u4_kernel, dim3(static_cast<uint32_t>(std::min<uint64_t>((n4 + 255) / 256, 1024))),
+                             dim3(256), 0, st, o4, n4);
   if (e != cudaSuccess) return e;
-  const uint32_t slices = (U + 255) / 256;
-  if (ctas <= 0) ctas = device_sm_count() * plain_ctas_per_sm();
+  const int nb = B == 1 ? 1 : (B == 2 ? 2 : 4);
+  const uint4* T4 = reinterpret_cast<const uint4*>(T);
+  if (ctas == 0 && plain_tma_ok(U, nb)) {
+    if (nb == 1) return launch_plain_tma<1, 8>(T4, n, U, R, words64, B, o4, st);
+    if (nb == 2) return launch_plain_tma<2, 8>(T4, n, U, R, words64, B, o4, st);
+    return launch_plain_tma<4, 4>(T4, n, U, R, words64, B, o4, st);
+  }
+  // register-streaming kernel for other row widths (ctas < 0 forces it)
+  const uint32_t slices = (U + kPlainSlice - 1) / kPlainSlice;
+  if (ctas <= 0)
+    ctas = device_sm_count() *
+           (nb == 1 ? plain_occupancy<1>() : nb == 2 ? plain_occupancy<2>() : plain_occupancy<4>());
   uint64_t chunks = static_cast<uint64_t>(ctas) / slices;
   if (chunks < 1) chunks = 1;
   if (chunks > n) chunks = n;
   const uint64_t rows_per_cta = (n + chunks - 1) / chunks;
   chunks = (n + rows_per_cta - 1) / rows_per_cta;
   dim3 grid(static_cast<uint32_t>(chunks), slices);
-  const uint4* T4 = reinterpret_cast<const uint4*>(T);
-  uint4* o4 = reinterpret_cast<uint4*>(out);
-  if (B == 1)
-    plain_scan_kernel<1, 8><<<grid, 256, 0, st>>>(T4, n, U, R, words64, B, o4, rows_per_cta);
-  else if (B == 2)
-    plain_scan_kernel<2, 8><<<grid, 256, 0, st>>>(T4, n, U, R, words64, B, o4, rows_per_cta);
-  else
-    plain_scan_kernel<4, 8><<<grid, 256, 0, st>>>(T4, n, U, R, words64, B, o4, rows_per_cta);
-  return cudaGetLastError();
+  if (nb == 1)
+    return launch_pdl(plain_scan_kernel<1, 8>, grid, dim3(256), 0, st, T4, n, U, R, words64, B, o4, rows_per_cta);
+  if (nb == 2)
+    return launch_pdl(plain_scan_kernel<2, 8>, grid, dim3(256), 0, st, T4, n, U, R, words64, B, o4, rows_per_cta);
+  return launch_pdl(plain_scan_kernel<4, 8>, grid, dim3(256), 0, st, T4, n, U, R, words64, B, o4, rows_per_cta);
 }
 
 int read_device_status_and_clear(int* status) {

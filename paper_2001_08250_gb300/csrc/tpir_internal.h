@@ -16,8 +16,19 @@ namespace tpir {
 // Batched scan (register-tiled GF(2) product), one persistent launch over a
 // list of jobs.  Each job is cut into items = (B-tile, W-tile, k-chunk).
 // ---------------------------------------------------------------------------
-constexpr int kConsumerWarps = 8;                    // compute warps per CTA
-constexpr int kScanThreads = 32 * (kConsumerWarps + 1);  // + 1 producer warp
+constexpr int kConsumerWarps = 8;                    // compute warps per CTA (2 warpgroups)
+constexpr int kProducerThreads = 128;                // 1 warpgroup: TMA issue + masks
+constexpr int kScanThreads = kProducerThreads + 32 * kConsumerWarps;  // 384
+// Register split (setmaxnreg): the CTA is launched with 384 x 168 registers;
+// the producer warpgroup gives registers back, the consumers take them:
+// 128 x 40 + 256 x 224 = 62464 <= 64512.  The launch is refused unless the
+// kernel was compiled to exactly kScanLaunchRegs registers per thread.
+constexpr int kScanLaunchRegs = 168;
+constexpr int kProducerRegs = 40;
+constexpr int kConsumerRegs = 224;
+static_assert(kProducerThreads * kProducerRegs + 32 * kConsumerWarps * kConsumerRegs <=
+                  kScanThreads * kScanLaunchRegs,
+              "register split exceeds the launch allocation");
 constexpr int kMR = 8;                               // requests per thread
 constexpr int kNW = 16;                              // 32-bit words per thread
 constexpr int kStages = 5;                           // smem pipeline depth
