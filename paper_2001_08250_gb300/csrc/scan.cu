@@ -103,11 +103,6 @@ __device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Named barrier of the producer warpgroup (id 1; id 0 is __syncthreads).
-__device__ __forceinline__ void producer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kProducerThreads) : "memory");
-}
-
 // 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
                                          uint64_t* bar) {
@@ -425,10 +420,6 @@ __device__ __forceinline__ Item decode_item(const ScanLaunch& L, uint32_t item) 
   return it;
 }
 
-__device__ __forceinline__ uint4 lds4(const uint32_t* p) {
-  return *reinterpret_cast<const uint4*>(p);
-}
-
 __device__ __forceinline__ void xor_row(uint32_t (&acc)[kMR][kNW], const uint4& m0, const uint4& m1,
                                         const uint4& t0, const uint4& t1, const uint4& t2,
                                         const uint4& t3) {
@@ -450,56 +441,42 @@ __device__ __forceinline__ uint4 lds4a(uint32_t addr) {
 }
 
 // One consumer warp's `nr` rows of a stage (rows first, first + wk, ...),
-// addressed by 32-bit shared-memory byte offsets; a thread's four 16-byte
-// table segments are SEG bytes apart.  Two operand sets (A, B) alternate: the
-// masks and table words of the next row are loaded while the current row's
-// 128 LOP3s run, and no register is copied between iterations.  (One code
-// path for every lane layout: per-layout copies of this loop overflow the
-// consumer register budget.)
+// addressed by 32-bit shared-memory byte offsets.  The masks and table words
+// of the next row are loaded while the current row's 128 LOP3s run (measured
+// faster on GB300 than two-rows-per-iteration or ping-pong operand sets).
+// LW_LOG2 fixes the lane layout so that a thread's four 16-byte segments sit
+// at immediate offsets.
+template <int LW_LOG2>
 __device__ __forceinline__ void consume_rows(uint32_t (&acc)[kMR][kNW], uint32_t ma, uint32_t ta,
-                                             uint32_t nr, uint32_t mstep, uint32_t tstep,
-                                             uint32_t SEG) {
+                                             uint32_t nr, uint32_t mstep, uint32_t tstep) {
+  constexpr uint32_t SEG = (1u << LW_LOG2) * 16u;
   if (nr == 0) return;
-  uint4 am0 = lds4a(ma), am1 = lds4a(ma + 16);
-  uint4 at0 = lds4a(ta), at1 = lds4a(ta + SEG), at2 = lds4a(ta + 2 * SEG), at3 = lds4a(ta + 3 * SEG);
-  uint4 bm0, bm1, bt0, bt1, bt2, bt3;
+  uint4 m0 = lds4a(ma), m1 = lds4a(ma + 16);
+  uint4 t0 = lds4a(ta), t1 = lds4a(ta + SEG), t2 = lds4a(ta + 2 * SEG), t3 = lds4a(ta + 3 * SEG);
   for (;;) {
-    if (nr > 1) {
+    if (--nr) {
       ma += mstep;
       ta += tstep;
-      bm0 = lds4a(ma);
-      bm1 = lds4a(ma + 16);
-      bt0 = lds4a(ta);
-      bt1 = lds4a(ta + SEG);
-      bt2 = lds4a(ta + 2 * SEG);
-      bt3 = lds4a(ta + 3 * SEG);
+      const uint4 n0 = lds4a(ma), n1 = lds4a(ma + 16);
+      const uint4 u0 = lds4a(ta), u1 = lds4a(ta + SEG), u2 = lds4a(ta + 2 * SEG), u3 = lds4a(ta + 3 * SEG);
+      xor_row(acc, m0, m1, t0, t1, t2, t3);
+      m0 = n0; m1 = n1; t0 = u0; t1 = u1; t2 = u2; t3 = u3;
+    } else {
+      xor_row(acc, m0, m1, t0, t1, t2, t3);
+      break;
     }
-    xor_row(acc, am0, am1, at0, at1, at2, at3);
-    if (--nr == 0) break;
-    if (nr > 1) {
-      ma += mstep;
-      ta += tstep;
-      am0 = lds4a(ma);
-      am1 = lds4a(ma + 16);
-      at0 = lds4a(ta);
-      at1 = lds4a(ta + SEG);
-      at2 = lds4a(ta + 2 * SEG);
-      at3 = lds4a(ta + 3 * SEG);
-    }
-    xor_row(acc, bm0, bm1, bt0, bt1, bt2, bt3);
-    if (--nr == 0) break;
   }
 }
 
 // One consumer warp's share of one item: wait for each stage, XOR its rows,
 // release the stage, then store (single k-chunk) or XOR-reduce (split) the
 // 8-request x 16-word register tile.  Returns false if a wait gave up.
+template <int LW_LOG2>
 __device__ __forceinline__ bool consume_item(const ScanJob& J, const Item& it, uint32_t cw,
                                              uint32_t lane, uint64_t* full, uint64_t* empty,
                                              uint8_t* stages, volatile int* abort_flag,
                                              uint32_t& iter) {
-  const uint32_t LW_LOG2 = J.shape.lw_log2;
-  const uint32_t LW = 1u << LW_LOG2;
+  constexpr uint32_t LW = 1u << LW_LOG2;
   const uint32_t ww = J.shape.ww, wbw = J.shape.wb * ww, wk = J.shape.wk;
   const uint32_t bt_ = J.shape.bt(), wt_ = J.shape.wt(), sr = J.shape.srows();
   const uint32_t wk_idx = cw / wbw, rem = cw % wbw;
@@ -524,7 +501,7 @@ __device__ __forceinline__ bool consume_item(const ScanJob& J, const Item& it, u
     const uint32_t rows = static_cast<uint32_t>(it.k1 - ks < sr ? it.k1 - ks : sr);
     const uint32_t nr = rows > wk_idx ? (rows - wk_idx + wk - 1) / wk : 0u;
     const uint32_t tbase = stage0 + s * kStageBytes;
-    consume_rows(acc, tbase + sr * wt_ * 4u + moff, tbase + toff, nr, mstep, tstep, LW * 16u);
+    consume_rows<LW_LOG2>(acc, tbase + sr * wt_ * 4u + moff, tbase + toff, nr, mstep, tstep);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -562,7 +539,6 @@ __global__ void __launch_bounds__(kScanThreads, 1)
   uint64_t* empty = full + kStages;
   uint8_t* stages = smem_raw + 256;
   __shared__ int s_abort;
-  __shared__ volatile int s_go[2];
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -600,9 +576,7 @@ __global__ void __launch_bounds__(kScanThreads, 1)
         // warpgroup waits on a hardware barrier instead of spinning.  The
         // outcome slot alternates with the stage parity so that a fast thread
         // 0 cannot overwrite it before the others have read it.
-        if (ptid == 0) s_go[iter & 1u] = mbar_wait_backoff(&empty[s], ph ^ 1u, abort_flag) ? 1 : 0;
-        producer_sync();
-        if (!s_go[iter & 1u]) {
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
           ok = false;
           break;
         }
@@ -647,7 +621,14 @@ __global__ void __launch_bounds__(kScanThreads, 1)
   for (uint32_t item = blockIdx.x; item < L.total_items; item += gridDim.x) {
     const Item it = decode_item(L, item);
     const ScanJob& J = L.jobs[it.job];
-    if (!consume_item(J, it, cw, lane, full, empty, stages, abort_flag, iter)) return;
+    bool ok;
+    switch (J.shape.lw_log2) {
+      case 5: ok = consume_item<5>(J, it, cw, lane, full, empty, stages, abort_flag, iter); break;
+      case 4: ok = consume_item<4>(J, it, cw, lane, full, empty, stages, abort_flag, iter); break;
+      case 3: ok = consume_item<3>(J, it, cw, lane, full, empty, stages, abort_flag, iter); break;
+      default: ok = consume_item<2>(J, it, cw, lane, full, empty, stages, abort_flag, iter); break;
+    }
+    if (!ok) return;
   }
 }
 

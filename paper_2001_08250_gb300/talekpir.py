@@ -97,7 +97,8 @@ def lib(path: str | None = None):
     """Load libtalekpir.so (building it first if the sources changed)."""
     global _lib
     if _lib is None:
-        p = path or _build.build()
+        # TALEKPIR_LIB selects a prebuilt library (e.g. another build variant)
+        p = path or os.environ.get("TALEKPIR_LIB") or _build.build()
         if not os.path.exists(p):
             raise RuntimeError(f"libtalekpir not found at {p}")
         L = ctypes.CDLL(p)
