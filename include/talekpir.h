@@ -108,6 +108,25 @@ tpir_status tpir_write(tpir_db *db, uint64_t b1, uint64_t b2, const void *msg,
 tpir_status tpir_write_batch(tpir_db *db, uint32_t count, const uint64_t *b1, const uint64_t *b2,
                              const void *msgs, tpir_status *status_out, uint32_t *evictions_out);
 
+/* A cuckoo write that allocates no device or pinned memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate, such
+ * as a serving thread for which a cudaMalloc (which may synchronise the whole
+ * device) is an unbounded stall, or a process whose device memory is all
+ * owned by another allocator under a hard budget.  Same placement rules and
+ * result as tpir_write, but the message d_msg is a DEVICE buffer of msg_bytes
+ * (16-byte aligned) that must stay valid until `stream` (a cudaStream_t, NULL
+ * = legacy default stream) reaches this write; the slot moves run on `stream`,
+ * after every read already submitted on this db and before every later read.
+ * Limits: msg_bytes <= 65536 and the db's max_evictions <= 500, else
+ * TPIR_EINVAL (nothing changes).  EFULL as for tpir_write.
+ * The moves use one temporary slot held in a 64 KiB device array that every
+ * GPU loading the library keeps until exit.  The first call on a device looks
+ * up that array's address, so make it before any stream capture.  All calls
+ * share the array: calls whose moves overlap on the GPU (writes to different
+ * dbs on different streams) race, so order them on one stream. */
+tpir_status tpir_write_noalloc(tpir_db *db, uint64_t b1, uint64_t b2, const void *d_msg,
+                               uint32_t *evictions_out, void *stream);
+
 /* ---- PIR reads (Section 2 step 5; batching as in Section 9.2) -------------
  * Synchronous: req_bits (host, B rows) in, out (host, B x row_bytes) out.
  * B = 0 is a no-op.  Sees every write made before the call. */

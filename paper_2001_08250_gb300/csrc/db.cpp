@@ -341,6 +341,7 @@ tpir_db* tpir_db_create(uint64_t n, uint32_t d, uint32_t msg_bytes) {
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&db->d_tmp), msg_bytes);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&db->last_write, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&db->stream_mark, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(db->last_write, db->stream);
   if (e != cudaSuccess) {
     set_error(cuda_status(e));
@@ -372,6 +373,7 @@ void tpir_db_destroy(tpir_db* db) {
   cudaFree(db->bloom.d_deltas);
   cudaFree(db->bloom.d_out);
   if (db->last_write) cudaEventDestroy(db->last_write);
+  if (db->stream_mark) cudaEventDestroy(db->stream_mark);
   if (db->stream) cudaStreamDestroy(db->stream);
   delete db->meta;
   delete db;

@@ -170,6 +170,7 @@ struct tpir_db {
   int forced_kernel = 0;
   cudaStream_t stream = nullptr;        // the db's own stream (writes, sync reads)
   cudaEvent_t last_write = nullptr;     // recorded after each write
+  cudaEvent_t stream_mark = nullptr;    // marks the db stream for foreign-stream writes
   std::vector<std::pair<cudaStream_t, cudaEvent_t>> read_events;  // async reads per stream
   tpir::CuckooMeta* meta = nullptr;
   // write staging of the db's own API calls

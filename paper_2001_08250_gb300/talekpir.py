@@ -68,6 +68,7 @@ _SIGS = [
     ("tpir_db_dump", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("tpir_write", ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     ("tpir_write_batch", ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
+    ("tpir_write_noalloc", ctypes.c_int, [_vp, _u64, _u64, _vp, _vp, _vp]),
     ("tpir_read_batch", ctypes.c_int, [_vp, _vp, _u32, _vp]),
     ("tpir_read_batch_async", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp]),
     ("tpir_db_set_kernel", ctypes.c_int, [_vp, ctypes.c_int]),
