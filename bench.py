@@ -158,9 +158,10 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--legs", default="head,plain,b32,e2e,serve,cpu",
+    ap.add_argument("--legs", default="head,plain,b32,e2e,serve,cpu,multi,large",
                     help="comma list of: head (B=256, timed headline), plain (B=1), b32, "
-                         "e2e (host buffers), serve, cpu (oracle baseline)")
+                         "e2e (host buffers), serve, cpu (oracle baseline), multi (64 uneven "
+                         "tables, one graph-captured launch), large (4 GiB table, B=1024)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
@@ -332,6 +333,9 @@ def main() -> None:
         cpu = {"value": sample / cdt, "unit": "reads/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample} reads of the 128 MiB table (single-threaded C)"}
 
+    multi = multi_leg(talekpir, synth, torch, stream, args) if "multi" in args.legs else None
+    large = large_leg(talekpir, torch, stream, args, hbm_peak) if "large" in args.legs else None
+
     gpu_launches = args.steps * ((USERS + B_HEAD - 1) // B_HEAD) * 2
     if rank == 0:
         line = {
@@ -351,6 +355,8 @@ def main() -> None:
             "legs": legs,
             "speedup_batched_vs_plain": value / legs["1"]["reads_per_s"],
             "serve": serve,
+            "multi_table": multi,
+            "large_table": large,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -358,6 +364,93 @@ def main() -> None:
         db.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _fill_random(db, nbytes, gen, torch, stream):
+    """Uniform random payload generated on the device (seeded), loaded in place."""
+    t = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device="cuda", generator=gen)
+    db.load_async(t, stream)
+    torch.cuda.synchronize()
+    del t
+
+
+def _events_ms(torch, stream, fn, reps):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def multi_leg(talekpir, synth, torch, stream, args) -> dict:
+    """64 uneven tables (n = 2^U(10,17) buckets, d in {2,4,8}, messages of
+    256/1024/4096 bytes, 16..512 reads each): all reads in ONE graph-captured
+    persistent launch, against 64 separate launches of the same kernel."""
+    shapes = synth.multi_table_shapes(64, seed=3)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    jobs, dbs, total_bytes, reads, ops = [], [], 0, 0, 0
+    for (n, d, z, B) in shapes:
+        db = talekpir.DB(n, d, z)
+        _fill_random(db, n * d * z, gen, torch, stream)
+        R = torch.randint(-(1 << 63), (1 << 63) - 1, (B, (n + 63) // 64), dtype=torch.int64,
+                          device="cuda", generator=gen)
+        O = torch.empty((B, d * z), dtype=torch.uint8, device="cuda")
+        jobs.append((db, B, R, O))
+        dbs.append(db)
+        total_bytes += n * d * z
+        reads += B
+        ops += B * n * d * z // 4
+    g = talekpir.MultiGraph(jobs)
+    for _ in range(args.warmup):
+        g.launch(stream)
+    graph_ms = _events_ms(torch, stream, lambda: g.launch(stream), max(3, args.steps))
+
+    def separate():
+        for (db, B, R, O) in jobs:
+            db.read_batch_async(R, B, O, stream)
+    for _ in range(2):
+        separate()
+    sep_ms = _events_ms(torch, stream, separate, max(2, args.steps // 2))
+    g.close()
+    for db in dbs:
+        db.close()
+    peak = alu_peak_tops(2070.0)
+    return {"tables": len(shapes), "table_bytes": total_bytes, "reads": reads,
+            "graph_ms": graph_ms, "separate_ms": sep_ms,
+            "reads_per_s_graph": reads / (graph_ms * 1e-3),
+            "reads_per_s_separate": reads / (sep_ms * 1e-3),
+            "lop3_tops_graph": ops / (graph_ms * 1e-3) / 1e12,
+            "lop3_frac_graph_at_2070MHz": ops / (graph_ms * 1e-3) / 1e12 / peak}
+
+
+def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:
+    """n = 2^20 buckets x 4 x 1 KiB (4 GiB): B = 1024 packed request rows in one
+    batched pass (the GF(2) product), and single plain reads (HBM stream)."""
+    n, d, z, B = 1 << 20, 4, 1024, 1024
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    db = talekpir.DB(n, d, z)
+    _fill_random(db, n * d * z, gen, torch, stream)
+    R = torch.randint(-(1 << 63), (1 << 63) - 1, (B, n // 64), dtype=torch.int64, device="cuda",
+                      generator=gen)
+    O = torch.empty((B, d * z), dtype=torch.uint8, device="cuda")
+    db.read_batch_async(R, B, O, stream)
+    bms = _events_ms(torch, stream, lambda: db.read_batch_async(R, B, O, stream), 3)
+    db.read_batch_async(R[:1], 1, O[:1], stream)
+    pms = _events_ms(torch, stream, lambda: db.read_batch_async(R[:1], 1, O[:1], stream), 16)
+    db.close()
+    ops = B * n * d * z // 4
+    tb = n * d * z
+    return {"n": n, "d": d, "msg_bytes": z, "B": B, "table_bytes": tb,
+            "batched_ms": bms, "batched_reads_per_s": B / (bms * 1e-3),
+            "batched_lop3_tops": ops / (bms * 1e-3) / 1e12,
+            "batched_lop3_frac_at_2070MHz": ops / (bms * 1e-3) / 1e12 / alu_peak_tops(2070.0),
+            "plain_ms": pms, "plain_reads_per_s": 1.0 / (pms * 1e-3),
+            "plain_scan_gbs": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9,
+            "plain_frac_hbm": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9 / hbm_peak}
 
 
 def serve_leg(talekpir, synth, rate: float, seconds: float) -> dict:

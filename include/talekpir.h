@@ -85,6 +85,9 @@ tpir_status tpir_db_set_policy(tpir_db *db, uint64_t capacity, uint32_t max_evic
  * table is then read-only content for the write path's purposes: later writes
  * treat every slot as free).  Synchronous. */
 tpir_status tpir_db_load(tpir_db *db, const void *host_table, size_t bytes);
+/* Asynchronous bulk load on `stream` from a device or pinned host buffer
+ * (same effect on metadata as tpir_db_load). */
+tpir_status tpir_db_load_async(tpir_db *db, const void *src, size_t bytes, void *stream);
 tpir_status tpir_db_dump(tpir_db *db, void *host_table, size_t bytes);
 
 /* ---- writes (Section 5.3, server steps 1-4) ------------------------------
@@ -157,6 +160,16 @@ typedef struct {
     void *d_out;
 } tpir_read_job;
 tpir_status tpir_read_multi_async(const tpir_read_job *jobs, uint32_t njobs, void *stream);
+
+/* The same many-table read captured once into a CUDA graph (one zero kernel
+ * and one persistent scan kernel), for workloads that repeat the launch with
+ * the same buffers.  tpir_graph_launch orders the replay after every write
+ * already made to the jobs' dbs.  The dbs and buffers must outlive the graph. */
+typedef struct tpir_graph tpir_graph;
+tpir_status tpir_read_multi_graph_create(const tpir_read_job *jobs, uint32_t njobs,
+                                         tpir_graph **out);
+tpir_status tpir_graph_launch(tpir_graph *g, void *stream);
+void tpir_graph_destroy(tpir_graph *g);
 
 /* Reads and clears the device-side status word that bounded waits inside the
  * kernels set when they give up (TPIR_OK or TPIR_ETIMEDOUT). Synchronises the

@@ -261,9 +261,12 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
     js.push_back(j);
   }
   if (js.empty()) return TPIR_OK;
-  const double target = total / (static_cast<double>(grid) * 4.0);
-  uint32_t items = 0;
-  for (auto& j : js) {
+  // ~8 items per CTA of about equal cost; jobs listed by descending item cost
+  // so that the kernel's snake order over items balances the CTAs
+  const double target = total / (static_cast<double>(grid) * 8.0);
+  std::vector<double> item_cost(js.size());
+  for (size_t i = 0; i < js.size(); ++i) {
+    ScanJob& j = js[i];
     const uint32_t sr = j.shape.srows();
     const double rc = row_cost(j);
     uint64_t rows = static_cast<uint64_t>(target / rc);
@@ -271,6 +274,15 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
     const uint64_t nmax = (j.n + sr - 1) / sr * sr;
     j.kc_rows = static_cast<uint32_t>(std::min<uint64_t>(rows, std::min<uint64_t>(nmax, 0xFFFFFFF0ull)));
     if (!finalize_job(j)) return TPIR_EINVAL;
+    item_cost[i] = static_cast<double>(std::min<uint64_t>(j.kc_rows, j.n)) * rc;
+  }
+  std::vector<size_t> order(js.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t a, size_t b) { return item_cost[a] > item_cost[b]; });
+  uint32_t items = 0;
+  for (size_t oi : order) {
+    ScanJob j = js[oi];
     j.item_begin = items;
     items += j.n_bt * j.n_wt * j.n_kc;
     L.jobs[L.njobs++] = j;
@@ -417,6 +429,19 @@ tpir_status tpir_db_load(tpir_db* db, const void* host_table, size_t bytes) {
   return TPIR_OK;
 }
 
+tpir_status tpir_db_load_async(tpir_db* db, const void* src, size_t bytes, void* stream) {
+  if (!db || !src || bytes != db->n * db->row_bytes) return TPIR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  order_writes_after_reads(db, st);
+  cudaError_t e = cudaEventRecord(db->stream_mark, db->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, db->stream_mark, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_table, src, bytes, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  db->meta->clear();
+  return TPIR_OK;
+}
+
 tpir_status tpir_db_dump(tpir_db* db, void* host_table, size_t bytes) {
   if (!db || !host_table || bytes != db->n * db->row_bytes) return TPIR_EINVAL;
   order_writes_after_reads(db, db->stream);
@@ -492,6 +517,59 @@ tpir_status tpir_read_multi_async(const tpir_read_job* jobs, uint32_t njobs, voi
   for (uint32_t i = 0; i < njobs; ++i)
     if (jobs[i].B) note_read(jobs[i].db, st);
   return TPIR_OK;
+}
+
+struct tpir_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<tpir_db*> dbs;
+};
+
+tpir_status tpir_read_multi_graph_create(const tpir_read_job* jobs, uint32_t njobs,
+                                         tpir_graph** out) {
+  if (!out || !jobs || njobs == 0 || njobs > TPIR_MAX_JOBS) return TPIR_EINVAL;
+  *out = nullptr;
+  for (uint32_t i = 0; i < njobs; ++i)
+    if (!jobs[i].db) return TPIR_EINVAL;
+  tpir_graph* g = new (std::nothrow) tpir_graph();
+  if (!g) return TPIR_ENOMEM;
+  (void)batched_grid();  // one-time kernel attributes, outside the capture
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  tpir_status s = TPIR_OK;
+  if (e == cudaSuccess) {
+    s = enqueue_multi(jobs, njobs, st);
+    cudaError_t e2 = cudaStreamEndCapture(st, &g->graph);
+    if (s == TPIR_OK && e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess && s == TPIR_OK) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (st) cudaStreamDestroy(st);
+  if (e != cudaSuccess || s != TPIR_OK) {
+    tpir_graph_destroy(g);
+    return s != TPIR_OK ? s : cuda_status(e);
+  }
+  for (uint32_t i = 0; i < njobs; ++i)
+    if (jobs[i].B) g->dbs.push_back(jobs[i].db);
+  *out = g;
+  return TPIR_OK;
+}
+
+tpir_status tpir_graph_launch(tpir_graph* g, void* stream) {
+  if (!g || !g->exec) return TPIR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (tpir_db* db : g->dbs) order_after_writes(db, st);
+  cudaError_t e = cudaGraphLaunch(g->exec, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (tpir_db* db : g->dbs) note_read(db, st);
+  return TPIR_OK;
+}
+
+void tpir_graph_destroy(tpir_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
 }
 
 tpir_status tpir_device_status(void) {

@@ -406,6 +406,13 @@ struct Item {
   uint64_t k0, k1;
 };
 
+// The r-th item of CTA c in snake order: round r takes items [r*G, (r+1)*G),
+// CTA c gets position c in even rounds and G-1-c in odd ones.  With items
+// listed by descending cost this balances uneven items across CTAs.
+__device__ __forceinline__ uint32_t snake_item(uint32_t r, uint32_t c, uint32_t G) {
+  return r * G + ((r & 1u) ? (G - 1u - c) : c);
+}
+
 __device__ __forceinline__ Item decode_item(const ScanLaunch& L, uint32_t item) {
   Item it;
   it.job = find_job(L, item);
@@ -562,7 +569,9 @@ __global__ void __launch_bounds__(kScanThreads, 1)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
     const uint32_t ptid = threadIdx.x;
     bool ok = true;
-    for (uint32_t item = blockIdx.x; ok && item < L.total_items; item += gridDim.x) {
+    for (uint32_t r = 0;; ++r) {
+      const uint32_t item = snake_item(r, blockIdx.x, gridDim.x);
+      if (!ok || item >= L.total_items) break;
       const Item it = decode_item(L, item);
       const ScanJob& J = L.jobs[it.job];
       const uint32_t bt_ = J.shape.bt(), wt_ = J.shape.wt(), sr = J.shape.srows();
@@ -618,7 +627,9 @@ __global__ void __launch_bounds__(kScanThreads, 1)
   // ---------------- consumer warpgroups ----------------
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
   const uint32_t cw = static_cast<uint32_t>(warp - kProducerThreads / 32);
-  for (uint32_t item = blockIdx.x; item < L.total_items; item += gridDim.x) {
+  for (uint32_t r = 0;; ++r) {
+    const uint32_t item = snake_item(r, blockIdx.x, gridDim.x);
+    if (item >= L.total_items) break;
     const Item it = decode_item(L, item);
     const ScanJob& J = L.jobs[it.job];
     bool ok;

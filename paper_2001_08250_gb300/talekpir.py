@@ -65,6 +65,7 @@ _SIGS = [
     ("tpir_db_info", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("tpir_db_set_policy", ctypes.c_int, [_vp, _u64, _u32, _u64]),
     ("tpir_db_load", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    ("tpir_db_load_async", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     ("tpir_db_dump", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("tpir_write", ctypes.c_int, [_vp, _u64, _u64, _vp, _vp]),
     ("tpir_write_batch", ctypes.c_int, [_vp, _u32, _vp, _vp, _vp, _vp, _vp]),
@@ -73,6 +74,9 @@ _SIGS = [
     ("tpir_read_batch_async", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp]),
     ("tpir_db_set_kernel", ctypes.c_int, [_vp, ctypes.c_int]),
     ("tpir_read_multi_async", ctypes.c_int, [_vp, _u32, _vp]),
+    ("tpir_read_multi_graph_create", ctypes.c_int, [_vp, _u32, _vp]),
+    ("tpir_graph_launch", ctypes.c_int, [_vp, _vp]),
+    ("tpir_graph_destroy", None, [_vp]),
     ("tpir_device_status", ctypes.c_int, []),
     ("tpir_bloom_create", ctypes.c_int, [_vp, _u64, _u32, _u32, _u32]),
     ("tpir_bloom_insert", ctypes.c_int, [_vp, _vp]),
@@ -204,6 +208,11 @@ class DB:
         t = np.ascontiguousarray(table, dtype=np.uint8)
         _check(lib().tpir_db_load(self.h, _hptr(t), t.nbytes), "tpir_db_load")
 
+    def load_async(self, src, stream=None) -> None:
+        """Bulk load from a device tensor (or pinned host tensor) of n*row_bytes bytes."""
+        _check(lib().tpir_db_load_async(self.h, src.data_ptr(), src.numel() * src.element_size(),
+                                        _stream(stream)), "tpir_db_load_async")
+
     def dump(self) -> np.ndarray:
         out = np.empty((self.n, self.row_bytes), dtype=np.uint8)
         _check(lib().tpir_db_dump(self.h, _hptr(out), out.nbytes), "tpir_db_dump")
@@ -280,6 +289,41 @@ def read_multi_async(jobs, stream=None) -> None:
         arr[i].d_req_bits = _dptr(d_req)
         arr[i].d_out = _dptr(d_out)
     _check(lib().tpir_read_multi_async(arr, len(jobs), _stream(stream)), "tpir_read_multi_async")
+
+
+def _jobs_array(jobs):
+    arr = (ReadJob * max(1, len(jobs)))()
+    for i, (db, B, d_req, d_out) in enumerate(jobs):
+        arr[i].db = db.h
+        arr[i].B = int(B)
+        arr[i].d_req_bits = _dptr(d_req)
+        arr[i].d_out = _dptr(d_out)
+    return arr
+
+
+class MultiGraph:
+    """A many-table read captured once into a CUDA graph; launch() replays it."""
+
+    def __init__(self, jobs):
+        self.jobs = jobs  # keep the buffers alive
+        h = _vp()
+        _check(lib().tpir_read_multi_graph_create(_jobs_array(jobs), len(jobs), ctypes.byref(h)),
+               "tpir_read_multi_graph_create")
+        self.h = h.value
+
+    def launch(self, stream=None) -> None:
+        _check(lib().tpir_graph_launch(self.h, _stream(stream)), "tpir_graph_launch")
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().tpir_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -175,3 +175,42 @@ def test_large_table_gf2_product_sampled():
         db.read_batch_async(dR, 4, dO1)
         assert np.array_equal(to_host(dO1), Out[:4])
     assert talekpir.device_status() == talekpir.OK
+
+
+def test_multi_table_graph_replays_see_writes():
+    """The many-table read captured into a CUDA graph: replays give the oracle's
+    replies, and a replay after a write to one table sees that write."""
+    torch = require_cuda()
+    shapes = [(1100, 2, 256, 16), (3000, 4, 1024, 40), (700, 8, 256, 64)]
+    dbs, jobs, Ts, Rs = [], [], [], []
+    for i, (n, d, z, B) in enumerate(shapes):
+        T = synth.table_bytes(n, d, z, seed=50, table=i)
+        R = synth.random_bits(B, n, seed=51, table=i)
+        db = _db(n, d, z, T)
+        dbs.append(db)
+        Ts.append(T)
+        Rs.append(R)
+        jobs.append((db, B, to_dev(R), dev_out(B, d * z)))
+    g = talekpir.MultiGraph(jobs)
+    for rep in range(2):
+        for (_, _, _, dO) in jobs:
+            dO.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        for (n, d, z, B), T, R, (_, _, _, dO) in zip(shapes, Ts, Rs, jobs):
+            assert np.array_equal(to_host(dO), oracle.read_batch(T, n, d, z, R)), rep
+    # a write to table 1, then a replay
+    n, d, z, B = shapes[1]
+    oc = oracle.Cuckoo(n, d, z, 0, 500, seed=0)
+    msg = synth.messages(1, z, seed=52)[0]
+    assert dbs[1].write(5, 6, msg)[0] == talekpir.OK   # table was bulk-loaded: every slot free
+    oc.insert(5, 6, msg)
+    T1 = Ts[1].copy()
+    T1[5, :z] = msg
+    g.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(jobs[1][3]), oracle.read_batch(T1, n, d, z, Rs[1]))
+    g.close()
+    for db in dbs:
+        db.close()
+    assert talekpir.device_status() == talekpir.OK
