@@ -3,6 +3,7 @@
 // here validates arguments, plans launches, moves buffers and keeps the
 // cuckoo metadata.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 
@@ -133,6 +134,11 @@ static ScanJob make_job(const tpir_db* db, const uint64_t* d_req, uint32_t B, vo
 
 static int batched_grid() { return device_sm_count() * batched_ctas_per_sm(); }
 
+uint32_t next_counter_slot() {
+  static std::atomic<uint32_t> next{0};
+  return next.fetch_add(1, std::memory_order_relaxed) % kItemCounterSlots;
+}
+
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
                          cudaStream_t st) {
   if (B == 0) return TPIR_OK;
@@ -160,6 +166,7 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
     if (!finalize_job(j)) return TPIR_EINVAL;
     L.jobs[0] = j;
     L.total_items = j.n_bt * j.n_wt * j.n_kc;
+    L.counter_slot = next_counter_slot();
     e = launch_zero_outputs(L, st);
     if (e == cudaSuccess)
       e = launch_batched(L, static_cast<int>(std::min<uint64_t>(L.total_items, grid)), st);
@@ -261,8 +268,8 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
     js.push_back(j);
   }
   if (js.empty()) return TPIR_OK;
-  // ~8 items per CTA of about equal cost; jobs listed by descending item cost
-  // so that the kernel's snake order over items balances the CTAs
+  // ~8 items per CTA of about equal cost; jobs listed by descending item cost,
+  // the order in which the kernel's CTAs claim them
   const double target = total / (static_cast<double>(grid) * 8.0);
   std::vector<double> item_cost(js.size());
   for (size_t i = 0; i < js.size(); ++i) {
@@ -288,6 +295,7 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
     L.jobs[L.njobs++] = j;
   }
   L.total_items = items;
+  L.counter_slot = next_counter_slot();
   cudaError_t e = launch_zero_outputs(L, st);
   if (e == cudaSuccess) e = launch_batched(L, static_cast<int>(std::min<uint32_t>(items, grid)), st);
   return cuda_status(e);

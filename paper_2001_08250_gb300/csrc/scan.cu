@@ -25,6 +25,11 @@ namespace tpir {
 // Device-side status word: set to TPIR_ETIMEDOUT by a bounded wait that gave up.
 __device__ int g_status;
 
+// Item counters of the batched kernel's dynamic schedule, one per launch in a
+// rotation of kItemCounterSlots: the zero kernel that precedes a launch resets
+// its slot, the launch's CTAs claim items from it.
+__device__ uint32_t g_item_counter[kItemCounterSlots];
+
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s: far above any legitimate wait
@@ -406,12 +411,6 @@ struct Item {
   uint64_t k0, k1;
 };
 
-// The r-th item of CTA c in snake order: round r takes items [r*G, (r+1)*G),
-// CTA c gets position c in even rounds and G-1-c in odd ones.  With items
-// listed by descending cost this balances uneven items across CTAs.
-__device__ __forceinline__ uint32_t snake_item(uint32_t r, uint32_t c, uint32_t G) {
-  return r * G + ((r & 1u) ? (G - 1u - c) : c);
-}
 
 __device__ __forceinline__ Item decode_item(const ScanLaunch& L, uint32_t item) {
   Item it;
@@ -544,8 +543,12 @@ __global__ void __launch_bounds__(kScanThreads, 1)
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* empty = full + kStages;
+  uint64_t* claim_full = empty + kStages;
+  uint64_t* claim_empty = claim_full + 1;
   uint8_t* stages = smem_raw + 256;
   __shared__ int s_abort;
+  __shared__ uint32_t s_claim;
+  __shared__ uint32_t s_hdr[kStages];
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -555,6 +558,8 @@ __global__ void __launch_bounds__(kScanThreads, 1)
       mbar_init(&full[s], kProducerThreads);
       mbar_init(&empty[s], kConsumerWarps);
     }
+    mbar_init(claim_full, 1);
+    mbar_init(claim_empty, kProducerThreads);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -565,13 +570,41 @@ __global__ void __launch_bounds__(kScanThreads, 1)
 
   if (threadIdx.x < kProducerThreads) {
     // ---------------- producer warpgroup ----------------
-    // warp 0 issues the bulk copies; all 128 threads expand request bits
+    // Thread 0 claims items (listed by descending cost) from the launch's
+    // counter and publishes each claim through claim_full; every producer
+    // thread acknowledges it on claim_empty before thread 0 may post the next
+    // one (so no waiter can miss a phase).  Warp 0 issues the bulk copies;
+    // all 128 threads expand request bits.  The claimed item id rides in the
+    // header of its first stage; once the items run out an END header
+    // releases the consumers.
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
     const uint32_t ptid = threadIdx.x;
+    uint32_t* counter = &g_item_counter[L.counter_slot];
     bool ok = true;
-    for (uint32_t r = 0;; ++r) {
-      const uint32_t item = snake_item(r, blockIdx.x, gridDim.x);
-      if (!ok || item >= L.total_items) break;
+    for (uint32_t r = 0; ok; ++r) {
+      if (ptid == 0) {
+        bool go = true;
+        if (r == 0)
+          pdl_wait();  // the previous kernel reset the counter
+        else
+          go = mbar_wait(claim_empty, (r - 1) & 1u, abort_flag);
+        if (go) {
+          s_claim = atomicAdd(counter, 1u);
+          mbar_arrive(claim_full);
+        }
+      }
+      if (!mbar_wait(claim_full, r & 1u, abort_flag)) break;
+      const uint32_t item = *reinterpret_cast<volatile uint32_t*>(&s_claim);
+      mbar_arrive(claim_empty);
+      if (item >= L.total_items) {
+        const uint32_t s = iter % kStages, ph = (iter / kStages) & 1u;
+        if (mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+          if (ptid == 0) s_hdr[s] = kEndItem;
+          mbar_arrive(&full[s]);
+        }
+        ++iter;
+        break;
+      }
       const Item it = decode_item(L, item);
       const ScanJob& J = L.jobs[it.job];
       const uint32_t bt_ = J.shape.bt(), wt_ = J.shape.wt(), sr = J.shape.srows();
@@ -581,10 +614,6 @@ __global__ void __launch_bounds__(kScanThreads, 1)
       for (uint64_t ks = it.k0; ks < it.k1; ks += sr, ++iter) {
         const uint32_t s = iter % kStages;
         const uint32_t ph = (iter / kStages) & 1u;
-        // one thread polls the slot's release and publishes the outcome; the
-        // warpgroup waits on a hardware barrier instead of spinning.  The
-        // outcome slot alternates with the stage parity so that a fast thread
-        // 0 cannot overwrite it before the others have read it.
         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
           ok = false;
           break;
@@ -592,11 +621,12 @@ __global__ void __launch_bounds__(kScanThreads, 1)
         uint32_t* tsm = reinterpret_cast<uint32_t*>(stages + s * kStageBytes);
         uint32_t* msm = tsm + sr * wt_;
         const uint32_t rows = static_cast<uint32_t>(it.k1 - ks < sr ? it.k1 - ks : sr);
+        if (ptid == 0 && ks == it.k0) s_hdr[s] = item;
         if (warp == 0) {
           if (lane == 0) mbar_expect_tx(&full[s], rows * wcount * 4u);
           __syncwarp();
-          for (uint32_t r = lane; r < rows; r += 32)
-            bulk_g2s(tsm + r * wt_, J.T + (ks + r) * J.Wd + w0, wcount * 4u, &full[s]);
+          for (uint32_t q = lane; q < rows; q += 32)
+            bulk_g2s(tsm + q * wt_, J.T + (ks + q) * J.Wd + w0, wcount * 4u, &full[s]);
         }
         // request bits -> 32-bit masks, zero for rows past the chunk and for
         // request slots past B
@@ -605,8 +635,8 @@ __global__ void __launch_bounds__(kScanThreads, 1)
           uint64_t wbits = 0;
           if (b0 + b < J.B) wbits = __ldg(J.R + static_cast<uint64_t>(b0 + b) * J.words64 + (ks >> 6));
           wbits >>= sh;
-          for (uint32_t r = 0; r < sr; ++r)
-            msm[r * bt_ + b] = (r < rows) ? bit_mask(wbits, r) : 0u;
+          for (uint32_t q = 0; q < sr; ++q)
+            msm[q * bt_ + b] = (q < rows) ? bit_mask(wbits, q) : 0u;
         }
         mbar_arrive(&full[s]);
       }
@@ -627,9 +657,12 @@ __global__ void __launch_bounds__(kScanThreads, 1)
   // ---------------- consumer warpgroups ----------------
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
   const uint32_t cw = static_cast<uint32_t>(warp - kProducerThreads / 32);
-  for (uint32_t r = 0;; ++r) {
-    const uint32_t item = snake_item(r, blockIdx.x, gridDim.x);
-    if (item >= L.total_items) break;
+  for (;;) {
+    // the header of the next item's first stage names the item (or END)
+    const uint32_t s = iter % kStages, ph = (iter / kStages) & 1u;
+    if (!mbar_wait(&full[s], ph, abort_flag)) return;
+    const uint32_t item = *reinterpret_cast<volatile uint32_t*>(&s_hdr[s]);
+    if (item == kEndItem) return;
     const Item it = decode_item(L, item);
     const ScanJob& J = L.jobs[it.job];
     bool ok;
@@ -655,11 +688,12 @@ __global__ void zero_u4_kernel(uint4* __restrict__ out, uint64_t n4) {
     out[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Zeroes the outputs of the jobs that are split over k-chunks (their CTAs
-// XOR-reduce into the output).  grid.y = job.
+// Resets the launch's item counter and zeroes the outputs of the jobs whose
+// partial replies are XOR-reduced.  grid.y = job.
 __global__ void zero_outputs_kernel(const __grid_constant__ ScanLaunch L) {
   pdl_launch_dependents();
   pdl_wait();
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) g_item_counter[L.counter_slot] = 0u;
   const ScanJob& J = L.jobs[blockIdx.y];
   if (!J.split) return;
   const uint64_t n4 = static_cast<uint64_t>(J.B) * J.Wd / 4;
@@ -800,8 +834,7 @@ cudaError_t launch_batched(const ScanLaunch& L, int grid, cudaStream_t st) {
 cudaError_t launch_zero_outputs(const ScanLaunch& L, cudaStream_t st) {
   bool any = false;
   for (uint32_t i = 0; i < L.njobs; ++i) any |= L.jobs[i].split != 0;
-  if (!any) return cudaSuccess;
-  return launch_pdl(zero_outputs_kernel, dim3(64, L.njobs), dim3(256), 0, st, L);
+  return launch_pdl(zero_outputs_kernel, dim3(any ? 64 : 1, L.njobs), dim3(256), 0, st, L);
 }
 
 template <int NB, int CPT>

@@ -66,11 +66,18 @@ struct ScanJob {
   uint32_t split;      // partial replies are XOR-reduced (n_kc > 1 or wk > 1)
 };
 
+constexpr uint32_t kItemCounterSlots = 256;  // launches with distinct item counters
+constexpr uint32_t kEndItem = 0xFFFFFFFFu;
+
 struct ScanLaunch {
   uint32_t njobs;
   uint32_t total_items;
+  uint32_t counter_slot;  // this launch's item counter (reset by the zero kernel)
+  uint32_t pad;
   ScanJob jobs[TPIR_MAX_JOBS];
 };
+// Assigns the next item-counter slot (rotating).
+uint32_t next_counter_slot();
 
 // Fills a job's tiling from its shape/k-chunking and validates smem fit.
 bool finalize_job(ScanJob& j);
