@@ -162,6 +162,8 @@ def main() -> None:
                     help="comma list of: head (B=256, timed headline), plain (B=1), b32, "
                          "e2e (host buffers), serve, cpu (oracle baseline), multi (64 uneven "
                          "tables, one graph-captured launch), large (4 GiB table, B=1024)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the tile-shape autotuner (use the built-in shape choice)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
@@ -251,6 +253,11 @@ def main() -> None:
         ms = start.elapsed_time(end) / steps
         durs = [a.elapsed_time(b) for evs in per_launch for a, b in evs]
         return ms, durs, ck
+
+    tune = None
+    if not args.no_autotune:
+        tune = dbs[0].autotune(B_HEAD, reps=3)
+        dbs[0].autotune(32, reps=3)
 
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
@@ -353,6 +360,7 @@ def main() -> None:
                                "unit": "GB/s", "frac": plain_gbs / hbm_peak, "traffic": None,
                                "kernel": "plain_scan_kernel", "peak_basis": "of measured" if peaks else "of fallback"},
             "legs": legs,
+            "autotune": tune,
             "speedup_batched_vs_plain": value / legs["1"]["reads_per_s"],
             "serve": serve,
             "multi_table": multi,
@@ -403,6 +411,17 @@ def multi_leg(talekpir, synth, torch, stream, args) -> dict:
         total_bytes += n * d * z
         reads += B
         ops += B * n * d * z // 4
+    tuned = 0
+    if not args.no_autotune:
+        # one trial per (row width, batch-size class), on the class's smallest table
+        seen = {}
+        for (db, B, R, O) in jobs:
+            key = (db.row_bytes, max(1, (B - 1).bit_length()))
+            if key not in seen or db.n < seen[key][0].n:
+                seen[key] = (db, B)
+        for db, B in seen.values():
+            db.autotune(B, reps=2)
+        tuned = len(seen)
     g = talekpir.MultiGraph(jobs)
     for _ in range(args.warmup):
         g.launch(stream)
@@ -419,6 +438,7 @@ def multi_leg(talekpir, synth, torch, stream, args) -> dict:
         db.close()
     peak = alu_peak_tops(2070.0)
     return {"tables": len(shapes), "table_bytes": total_bytes, "reads": reads,
+            "tuned_classes": tuned,
             "graph_ms": graph_ms, "separate_ms": sep_ms,
             "reads_per_s_graph": reads / (graph_ms * 1e-3),
             "reads_per_s_separate": reads / (sep_ms * 1e-3),

@@ -149,6 +149,26 @@ tpir_status tpir_read_batch_async(tpir_db *db, const uint64_t *d_req_bits, uint3
  * streaming only (the path used for row widths the TMA-staged one skips). */
 tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
 
+/* Autotuner of the batched kernel's tile shape: times every admissible shape
+ * (lanes along the row, warps along requests / row / buckets, i.e. the batch
+ * tile width and the row tile width, and the rows per pipeline stage) for
+ * this table's row width and a batch of B requests, on the table itself, and
+ * keeps the fastest for every later launch of that row width and batch-size
+ * class (ceil(log2 B)).  reps = timed launches per shape (0 = 3).  Allocates
+ * scratch buffers for the trial requests and replies. */
+typedef struct {
+    uint32_t lw_log2, warps_b, warps_w, warps_k, stage_rows;
+    uint32_t tile_b, tile_w;   /* requests and 32-bit words per CTA tile */
+    uint32_t candidates;       /* shapes timed */
+    double us_per_launch;      /* of the chosen shape */
+    double lop3_tops;          /* B*n*row_words / time */
+} tpir_tune_result;
+tpir_status tpir_autotune(tpir_db *db, uint32_t B, uint32_t reps, tpir_tune_result *out);
+/* The tuned shapes as JSON (one plan per line), and back; clear forgets them. */
+tpir_status tpir_tune_save(const char *path);
+tpir_status tpir_tune_load(const char *path);
+tpir_status tpir_tune_clear(void);
+
 /* Many tables in ONE persistent launch (the uneven-batching workload): job i
  * reads B_i rows of d_req_bits_i against db_i into d_out_i.  Tables may differ
  * in n, d and msg_bytes.  Up to TPIR_MAX_JOBS jobs per call. */

@@ -96,7 +96,7 @@ static double row_cost(const ScanJob& j) {
 
 // Chooses kc_rows for one job so that items fill `grid` CTAs with the least
 // makespan (rounds of items x rows per item).
-static void plan_single(ScanJob& j, int grid) {
+void plan_single(ScanJob& j, int grid) {
   const uint32_t sr = j.shape.srows();
   const uint64_t tiles = static_cast<uint64_t>((j.B + j.shape.bt() - 1) / j.shape.bt()) *
                          ((j.Wd + j.shape.wt() - 1) / j.shape.wt());
@@ -119,7 +119,7 @@ static void plan_single(ScanJob& j, int grid) {
   j.kc_rows = best_rows;
 }
 
-static ScanJob make_job(const tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out) {
+ScanJob make_job(const tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out) {
   ScanJob j{};
   j.T = reinterpret_cast<const uint32_t*>(db->d_table);
   j.R = d_req;
@@ -128,11 +128,11 @@ static ScanJob make_job(const tpir_db* db, const uint64_t* d_req, uint32_t B, vo
   j.Wd = db->Wd;
   j.words64 = db->words64;
   j.B = B;
-  j.shape = choose_shape(db->Wd, B);
+  if (!plan_lookup(db->Wd, B, &j.shape)) j.shape = choose_shape(db->Wd, B);
   return j;
 }
 
-static int batched_grid() { return device_sm_count() * batched_ctas_per_sm(); }
+int batched_grid() { return device_sm_count() * batched_ctas_per_sm(); }
 
 uint32_t next_counter_slot() {
   static std::atomic<uint32_t> next{0};

@@ -82,6 +82,9 @@ uint32_t next_counter_slot();
 // Fills a job's tiling from its shape/k-chunking and validates smem fit.
 bool finalize_job(ScanJob& j);
 Shape choose_shape(uint32_t Wd, uint32_t B);
+// Tuned shapes (plan.cpp): the shape the autotuner measured fastest for a
+// row width and a batch-size class, if any.
+bool plan_lookup(uint32_t Wd, uint32_t B, Shape* out);
 int scan_stage_bytes(const Shape& s);
 
 // Launch helpers (scan.cu).  All return cudaError_t of the launch.
@@ -213,4 +216,7 @@ void order_writes_after_reads(tpir_db* db, cudaStream_t st);
 bool grow_dev(void** p, uint64_t* cap, uint64_t need);
 bool grow_pinned(void** p, uint64_t* cap, uint64_t need);
 uint64_t db_device_bytes(uint64_t n, uint32_t d, uint32_t z);
+ScanJob make_job(const tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out);
+void plan_single(ScanJob& j, int grid);
+int batched_grid();
 }  // namespace tpir

@@ -41,6 +41,15 @@ class ServeConfig(ctypes.Structure):
                 ("queue_capacity", _u32), ("tick_us", _u32)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("lw_log2", _u32), ("warps_b", _u32), ("warps_w", _u32), ("warps_k", _u32),
+                ("stage_rows", _u32), ("tile_b", _u32), ("tile_w", _u32), ("candidates", _u32),
+                ("us_per_launch", ctypes.c_double), ("lop3_tops", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Completion(ctypes.Structure):
     _fields_ = [("tag", _u64), ("status", _i32), ("kind", _u32), ("table_id", _u32),
                 ("evictions", _u32), ("epoch", _u64), ("t_arrive_ns", _i64),
@@ -74,6 +83,10 @@ _SIGS = [
     ("tpir_read_batch_async", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp]),
     ("tpir_db_set_kernel", ctypes.c_int, [_vp, ctypes.c_int]),
     ("tpir_read_multi_async", ctypes.c_int, [_vp, _u32, _vp]),
+    ("tpir_autotune", ctypes.c_int, [_vp, _u32, _u32, _vp]),
+    ("tpir_tune_save", ctypes.c_int, [ctypes.c_char_p]),
+    ("tpir_tune_load", ctypes.c_int, [ctypes.c_char_p]),
+    ("tpir_tune_clear", ctypes.c_int, []),
     ("tpir_read_multi_graph_create", ctypes.c_int, [_vp, _u32, _vp]),
     ("tpir_graph_launch", ctypes.c_int, [_vp, _vp]),
     ("tpir_graph_destroy", None, [_vp]),
@@ -257,6 +270,12 @@ class DB:
         _check(lib().tpir_read_batch_async(self.h, _dptr(d_req), int(B), _dptr(d_out),
                                            _stream(stream)), "tpir_read_batch_async")
 
+    def autotune(self, B: int, reps: int = 3) -> dict:
+        """Time every tile shape for B requests on this table; keep the fastest."""
+        r = TuneResult()
+        _check(lib().tpir_autotune(self.h, int(B), int(reps), ctypes.byref(r)), "tpir_autotune")
+        return r.as_dict()
+
     # -- interest vector -------------------------------------------------------
     def bloom_create(self, m_bits: int, k: int, window: int = 1, writes_per_delta: int = 0) -> None:
         self.bloom_m, self.bloom_k = int(m_bits), int(k)
@@ -278,6 +297,18 @@ class DB:
         out = np.empty((self.bloom_m + 63) // 64, dtype=np.uint64)
         _check(lib().tpir_bloom_get(self.h, _hptr(out)), "tpir_bloom_get")
         return out
+
+
+def tune_save(path: str) -> None:
+    _check(lib().tpir_tune_save(path.encode()), "tpir_tune_save")
+
+
+def tune_load(path: str) -> None:
+    _check(lib().tpir_tune_load(path.encode()), "tpir_tune_load")
+
+
+def tune_clear() -> None:
+    _check(lib().tpir_tune_clear(), "tpir_tune_clear")
 
 
 def read_multi_async(jobs, stream=None) -> None:

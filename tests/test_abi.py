@@ -63,3 +63,35 @@ def test_invalid_arguments_rejected_before_any_device_work():
     assert L.tpir_db_create(16, 0, 1024) is None
     assert L.tpir_read_batch(None, None, 1, None) == talekpir.EINVAL
     assert L.tpir_read_multi_async(None, 200, None) == talekpir.EINVAL
+
+
+def test_tuned_plans_round_trip_through_json(tmp_path):
+    from paper_2001_08250_gb300 import talekpir
+    good = tmp_path / "plans.json"
+    good.write_text(
+        '{"plans": [\n'
+        '{"row_words": 1024, "batch_class": 8, "lw_log2": 5, "warps_b": 8, "warps_w": 1, "warps_k": 1, "stage_rows_log2": 3},\n'
+        '{"row_words": 128, "batch_class": 5, "lw_log2": 3, "warps_b": 1, "warps_w": 1, "warps_k": 8, "stage_rows_log2": 4}\n'
+        ']}\n')
+    talekpir.tune_clear()
+    talekpir.tune_load(str(good))
+    out = tmp_path / "out.json"
+    talekpir.tune_save(str(out))
+    text = out.read_text()
+    assert '"row_words": 1024, "batch_class": 8, "lw_log2": 5, "warps_b": 8' in text
+    assert '"row_words": 128, "batch_class": 5, "lw_log2": 3' in text
+    # shapes the kernel cannot run are refused (warps do not multiply to 8;
+    # a stage larger than the ring slot)
+    bad = tmp_path / "bad.json"
+    bad.write_text(
+        '{"plans": [\n'
+        '{"row_words": 64, "batch_class": 3, "lw_log2": 5, "warps_b": 2, "warps_w": 2, "warps_k": 1, "stage_rows_log2": 0},\n'
+        '{"row_words": 64, "batch_class": 4, "lw_log2": 5, "warps_b": 1, "warps_w": 8, "warps_k": 1, "stage_rows_log2": 5}\n'
+        ']}\n')
+    import pytest
+    with pytest.raises(talekpir.TpirError):
+        talekpir.tune_load(str(bad))
+    talekpir.tune_clear()
+    empty = tmp_path / "empty.json"
+    talekpir.tune_save(str(empty))
+    assert '"row_words"' not in empty.read_text()

@@ -214,3 +214,19 @@ def test_multi_table_graph_replays_see_writes():
     for db in dbs:
         db.close()
     assert talekpir.device_status() == talekpir.OK
+
+
+def test_autotuned_shape_stays_bit_exact():
+    """The autotuner times every tile shape on the table; the shape it keeps
+    is used by later launches, which must still match the oracle."""
+    require_cuda()
+    n, d, z, B = 4100, 2, 512, 100
+    T = synth.table_bytes(n, d, z, seed=60)
+    R = synth.random_bits(B, n, seed=61)
+    with _db(n, d, z, T) as db:
+        res = db.autotune(B, reps=2)
+        assert res["candidates"] >= 2 and res["us_per_launch"] > 0
+        assert res["warps_b"] * res["warps_w"] * res["warps_k"] == 8
+        db.set_kernel(BATCHED)
+        assert np.array_equal(db.read_batch(R), oracle.read_batch(T, n, d, z, R))
+    talekpir.tune_clear()
