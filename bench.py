@@ -161,10 +161,15 @@ def main() -> None:
     ap.add_argument("--legs", default="head,plain,b32,e2e,serve,cpu,multi,large",
                     help="comma list of: head (B=256, timed headline), plain (B=1), b32, "
                          "e2e (host buffers), serve, cpu (oracle baseline), multi (64 uneven "
-                         "tables, one graph-captured launch), large (4 GiB table, B=1024)")
+                         "tables, one graph-captured launch), large (4 GiB table, B=1024); "
+                         "serve_sweep (not default: tables filling a 64 GiB budget, Poisson "
+                         "arrivals at --sweep-rates)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the tile-shape autotuner (use the built-in shape choice)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--sweep-rates", default="5000,10000,20000,50000",
+                    help="read arrival rates of the serve_sweep leg")
+    ap.add_argument("--sweep-seconds", type=float, default=6.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -340,6 +345,9 @@ def main() -> None:
         cpu = {"value": sample / cdt, "unit": "reads/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample} reads of the 128 MiB table (single-threaded C)"}
 
+    sweep = None
+    if "serve_sweep" in args.legs and rank == 0:
+        sweep = serve_sweep_leg(talekpir, synth, torch, stream, args)
     multi = multi_leg(talekpir, synth, torch, stream, args) if "multi" in args.legs else None
     large = large_leg(talekpir, torch, stream, args, hbm_peak) if "large" in args.legs else None
 
@@ -364,6 +372,7 @@ def main() -> None:
             "speedup_batched_vs_plain": value / legs["1"]["reads_per_s"],
             "serve": serve,
             "multi_table": multi,
+            "serve_sweep": sweep,
             "large_table": large,
             "cpu_baseline": cpu,
         }
@@ -471,6 +480,90 @@ def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:
             "plain_ms": pms, "plain_reads_per_s": 1.0 / (pms * 1e-3),
             "plain_scan_gbs": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9,
             "plain_frac_hbm": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9 / hbm_peak}
+
+
+def _drive(srv, talekpir, synth, tids, sizes, reqs, msgs, rate, seconds, seed, m_bits, k):
+    """Open-loop Poisson ops at `rate` reads/s plus 10% writes (each with k
+    interest-vector positions); latency from each op's scheduled arrival."""
+    import threading
+    count = int(rate / 0.9 * seconds)
+    arr = synth.poisson_arrivals(rate / 0.9, count, seed=seed)
+    is_w = synth.op_mix(count, 0.1, seed=seed)
+    tsel = (synth.stream(synth.stream_key(seed, 99), count) % np.uint64(len(tids))).astype(np.int64)
+    keys = synth.write_keys(count, seed=seed + 1)
+    outs = [np.empty(4096, dtype=np.uint8) for _ in range(4096)]
+    done = [0]
+
+    def poller():
+        while done[0] < count:
+            done[0] += len(srv.poll())
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.monotonic_ns()
+    for i in range(count):
+        ta = t0 + int(arr[i] * 1e9)
+        while time.monotonic_ns() < ta:
+            pass
+        t = int(tsel[i])
+        if is_w[i]:
+            b1, b2 = synth.bucket_pairs(keys[i:i + 1], sizes[t])
+            pos = synth.bloom_positions(keys[i:i + 1], m_bits, k)[0]
+            while srv.submit_write(tids[t], int(b1[0]), int(b2[0]), msgs[i % len(msgs)], i, pos,
+                                   ta) == talekpir.EAGAIN:
+                time.sleep(0.0001)
+        else:
+            while srv.submit_read(tids[t], reqs[t][i % len(reqs[t])], outs[i % 4096], i,
+                                  ta) == talekpir.EAGAIN:
+                time.sleep(0.0001)
+    srv.drain()
+    th.join()
+    return count
+
+
+def serve_sweep_leg(talekpir, synth, torch, stream, args) -> dict:
+    """Serving under a 64 GiB HBM budget: tables of 2^15..2^18 buckets x 4 x
+    1 KiB are added until the budget refuses one; then open-loop Poisson reads
+    at each rate of --sweep-rates with 10% writes (max 500 evictions, k = 4
+    interest-vector positions in m = 2^20 bits)."""
+    m_bits, k = 1 << 20, 4
+    srv = talekpir.Server(hbm_budget_bytes=64 << 30, max_batch=256, max_inflight=2)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    sizes, tids = [], []
+    cycle = [1 << 15, 1 << 16, 1 << 17, 1 << 18]
+    t_fill = time.perf_counter()
+    while True:
+        n = cycle[len(tids) % 4]
+        try:
+            tid = srv.add_table(n, 4, 1024)
+        except talekpir.TpirError:
+            break
+        db = srv.table(tid)
+        _fill_random(db, n * 4096, gen, torch, stream)
+        db.bloom_create(m_bits, k, window=4, writes_per_delta=1000)
+        sizes.append(n)
+        tids.append(tid)
+    t_fill = time.perf_counter() - t_fill
+    reqs = [synth.random_bits(16, n, seed=7, table=i) for i, n in enumerate(sizes)]
+    msgs = synth.messages(64, 1024, seed=8)
+    rates = [float(x) for x in args.sweep_rates.split(",") if x]
+    res = []
+    for rate in rates:
+        srv.reset_stats()
+        ops = _drive(srv, talekpir, synth, tids, sizes, reqs, msgs, rate, args.sweep_seconds,
+                     seed=int(rate), m_bits=m_bits, k=k)
+        st = srv.stats()
+        res.append({"offered_reads_per_s": rate, "reads_per_s": st.reads_per_s,
+                    "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms,
+                    "reads": st.reads_done, "writes": st.writes_done, "failed": st.failed,
+                    "rejected": st.rejected, "launches": st.launches,
+                    "mean_batch": st.mean_batch, "ops": ops})
+    total = int(sum(n * 4096 for n in sizes))
+    srv.close()
+    return {"tables": len(sizes), "table_bytes": total, "hbm_budget": 64 << 30,
+            "fill_s": t_fill, "seconds_per_rate": args.sweep_seconds, "rates": res}
 
 
 def serve_leg(talekpir, synth, rate: float, seconds: float) -> dict:

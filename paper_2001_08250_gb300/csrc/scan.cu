@@ -611,6 +611,13 @@ __global__ void __launch_bounds__(kScanThreads, 1)
       const uint32_t w0 = it.wt * wt_;
       const uint32_t wcount = min(wt_, J.Wd - w0);
       const uint32_t b0 = it.bt * bt_;
+      // a tile spanning whole rows is contiguous in global and shared memory
+      const bool whole_rows = (wt_ == J.Wd);
+      // each thread's request words (b = ptid + 128 c, c < 4; a B-tile holds at
+      // most 512 requests): one 64-bit word
+      // covers 64 buckets, i.e. several stages, so it is loaded once per word
+      uint64_t wcache[4] = {0, 0, 0, 0};
+      uint64_t widx = ~0ull;
       for (uint64_t ks = it.k0; ks < it.k1; ks += sr, ++iter) {
         const uint32_t s = iter % kStages;
         const uint32_t ph = (iter / kStages) & 1u;
@@ -625,18 +632,34 @@ __global__ void __launch_bounds__(kScanThreads, 1)
         if (warp == 0) {
           if (lane == 0) mbar_expect_tx(&full[s], rows * wcount * 4u);
           __syncwarp();
-          for (uint32_t q = lane; q < rows; q += 32)
-            bulk_g2s(tsm + q * wt_, J.T + (ks + q) * J.Wd + w0, wcount * 4u, &full[s]);
+          if (whole_rows) {
+            if (lane == 0) bulk_g2s(tsm, J.T + ks * J.Wd, rows * wcount * 4u, &full[s]);
+          } else {
+            for (uint32_t q = lane; q < rows; q += 32)
+              bulk_g2s(tsm + q * wt_, J.T + (ks + q) * J.Wd + w0, wcount * 4u, &full[s]);
+          }
         }
         // request bits -> 32-bit masks, zero for rows past the chunk and for
         // request slots past B
+        if ((ks >> 6) != widx) {
+          widx = ks >> 6;
+#pragma unroll
+          for (uint32_t c = 0; c < 4; ++c) {
+            const uint32_t b = ptid + c * kProducerThreads;
+            wcache[c] = (b < bt_ && b0 + b < J.B)
+                            ? __ldg(J.R + static_cast<uint64_t>(b0 + b) * J.words64 + widx)
+                            : 0ull;
+          }
+        }
         const uint32_t sh = static_cast<uint32_t>(ks & 63);
-        for (uint32_t b = ptid; b < bt_; b += kProducerThreads) {
-          uint64_t wbits = 0;
-          if (b0 + b < J.B) wbits = __ldg(J.R + static_cast<uint64_t>(b0 + b) * J.words64 + (ks >> 6));
-          wbits >>= sh;
-          for (uint32_t q = 0; q < sr; ++q)
-            msm[q * bt_ + b] = (q < rows) ? bit_mask(wbits, q) : 0u;
+#pragma unroll
+        for (uint32_t c = 0; c < 4; ++c) {
+          const uint32_t b = ptid + c * kProducerThreads;
+          if (b < bt_) {
+            const uint64_t wbits = wcache[c] >> sh;
+            for (uint32_t q = 0; q < sr; ++q)
+              msm[q * bt_ + b] = (q < rows) ? bit_mask(wbits, q) : 0u;
+          }
         }
         mbar_arrive(&full[s]);
       }

@@ -8,8 +8,9 @@
 //   - a worker thread forms a launch whenever a pipeline slot is free: it
 //     scans the FIFO in arrival order, applies each table's writes (host
 //     placement + device moves) and collects up to max_batch reads per table;
-//     all collected reads of all tables run in ONE persistent launch of the
-//     batched scan kernel, after the writes of that launch (stream order);
+//     the collected reads run after the writes of that launch (stream
+//     order): tables with a few reads stream through the plain kernel, all
+//     others share ONE persistent launch of the batched scan kernel;
 //   - up to max_inflight launches are queued on the device at once, with their
 //     request/reply copies on a copy stream overlapping the running kernels,
 //     so reads that arrive while others are on the GPU join the next launch;
@@ -31,6 +32,9 @@
 namespace {
 
 using namespace tpir;
+
+// Tables with at most this many reads in a launch use the plain kernel.
+constexpr uint32_t kServePlainMaxB = 4;
 
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -329,7 +333,18 @@ bool form_launch(tpir_server* s, int si) {
     cudaMemcpyAsync(sl.d_req, sl.h_req, req_words * 8, cudaMemcpyHostToDevice, s->copy);
     cudaEventRecord(sl.h2d_done, s->copy);
     cudaStreamWaitEvent(s->compute, sl.h2d_done, 0);
-    enqueue_multi(jobs.data(), static_cast<uint32_t>(jobs.size()), s->compute);
+    // tables with a few reads are HBM-bound: stream each with the plain
+    // kernel (back-to-back launches overlap); the rest share one persistent
+    // launch of the batched kernel
+    std::vector<tpir_read_job> batched;
+    for (const tpir_read_job& j : jobs) {
+      if (j.B <= kServePlainMaxB)
+        enqueue_read(j.db, j.d_req_bits, j.B, j.d_out, s->compute);
+      else
+        batched.push_back(j);
+    }
+    if (!batched.empty())
+      enqueue_multi(batched.data(), static_cast<uint32_t>(batched.size()), s->compute);
     cudaEventRecord(sl.kern_done, s->compute);
     cudaStreamWaitEvent(s->copy, sl.kern_done, 0);
     cudaMemcpyAsync(sl.h_out, sl.d_out, out_bytes, cudaMemcpyDeviceToHost, s->copy);

@@ -21,18 +21,19 @@ constexpr int kProducerThreads = 128;                // 1 warpgroup: TMA issue +
 constexpr int kScanThreads = kProducerThreads + 32 * kConsumerWarps;  // 384
 // Register split (setmaxnreg): the CTA is launched with 384 x 168 registers;
 // the producer warpgroup gives registers back, the consumers take them:
-// 128 x 40 + 256 x 224 = 62464 <= 64512.  The launch is refused unless the
-// kernel was compiled to exactly kScanLaunchRegs registers per thread.
+// 128 x 56 + 256 x 224 = 64512 = 384 x 168 (an exact fit).  The launch is
+// refused unless the kernel was compiled to exactly kScanLaunchRegs registers
+// per thread.
 constexpr int kScanLaunchRegs = 168;
-constexpr int kProducerRegs = 40;
+constexpr int kProducerRegs = 56;
 constexpr int kConsumerRegs = 224;
 static_assert(kProducerThreads * kProducerRegs + 32 * kConsumerWarps * kConsumerRegs <=
                   kScanThreads * kScanLaunchRegs,
               "register split exceeds the launch allocation");
 constexpr int kMR = 8;                               // requests per thread
 constexpr int kNW = 16;                              // 32-bit words per thread
-constexpr int kStages = 5;                           // smem pipeline depth
-constexpr int kStageBytes = 20 * 1024;               // table tile + masks, per stage
+constexpr int kStages = 6;                           // smem pipeline depth
+constexpr int kStageBytes = 36 * 1024;               // table tile + masks, per stage
 constexpr int kScanSmem = kStages * kStageBytes + 256;
 
 // Warp layout of a CTA tile: LW lanes along the row (W), 32/LW lanes along
