@@ -40,6 +40,11 @@ B_HEAD = 256
 COPIES = 4
 HBM_PEAK_FALLBACK = 6800.0
 SMS, LOP3_PER_CLK_PER_SM = 152, 64
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
+# this workload (profiles/batched_scan_kernel_paper_scale_B256.md,
+# profiles/plain_tma_kernel_paper_scale_B1.md)
+TRAFFIC_BATCHED_B256 = 136.424704e6 + 3.473152e6
+TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
 
 
 def measured_peaks() -> dict:
@@ -361,11 +366,13 @@ def main() -> None:
             "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": ck,
             "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
-                         "unit": "Top/s", "frac": achieved_tops / peak_tops, "traffic": None,
+                         "unit": "Top/s", "frac": achieved_tops / peak_tops,
+                         "traffic": TRAFFIC_BATCHED_B256,
                          "kernel": "batched_scan_kernel (+ zero_outputs_kernel)",
                          "peak_basis": f"{SMS} SMs x {LOP3_PER_CLK_PER_SM} LOP3/clk x {sm_mhz:.0f} MHz (median SM clock sampled)"},
             "roofline_plain": {"bound": "hbm", "achieved": plain_gbs, "peak": hbm_peak,
-                               "unit": "GB/s", "frac": plain_gbs / hbm_peak, "traffic": None,
+                               "unit": "GB/s", "frac": plain_gbs / hbm_peak,
+                               "traffic": TRAFFIC_PLAIN_B1,
                                "kernel": "plain_scan_kernel", "peak_basis": "of measured" if peaks else "of fallback"},
             "legs": legs,
             "autotune": tune,

@@ -191,6 +191,13 @@ tpir_status tpir_read_multi_graph_create(const tpir_read_job *jobs, uint32_t njo
 tpir_status tpir_graph_launch(tpir_graph *g, void *stream);
 void tpir_graph_destroy(tpir_graph *g);
 
+/* Self-test of failure detection (no counterpart in the paper): runs one CTA
+ * whose bounded wait, on a barrier nothing arrives at, gives up after
+ * limit_us microseconds (1..1000000) exactly as the scan kernels' waits do;
+ * returns the status word it left (TPIR_ETIMEDOUT expected), cleared, with the
+ * CUDA context still usable. */
+tpir_status tpir_selftest_wait_timeout(uint32_t limit_us);
+
 /* Reads and clears the device-side status word that bounded waits inside the
  * kernels set when they give up (TPIR_OK or TPIR_ETIMEDOUT). Synchronises the
  * device. */

@@ -580,6 +580,16 @@ void tpir_graph_destroy(tpir_graph* g) {
   delete g;
 }
 
+tpir_status tpir_selftest_wait_timeout(uint32_t limit_us) {
+  if (limit_us == 0 || limit_us > 1000000) return TPIR_EINVAL;
+  cudaError_t e = launch_selftest_wait(static_cast<uint64_t>(limit_us) * 1000ull, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = 0;
+  if (read_device_status_and_clear(&st) != 0) return TPIR_ECUDA;
+  return st ? static_cast<tpir_status>(st) : TPIR_OK;
+}
+
 tpir_status tpir_device_status(void) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_status(e);

@@ -75,13 +75,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits for the phase of `parity` to complete.  Gives up (returns false) after
-// kWaitLimitNs or when another warp of the CTA has given up already.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// limit_ns or when another warp of the CTA has given up already; giving up
+// sets the CTA's abort flag and the device status word.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitLimitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicExch(&g_status, (int)TPIR_ETIMEDOUT);
       return false;
@@ -726,7 +728,28 @@ __global__ void zero_outputs_kernel(const __grid_constant__ ScanLaunch L) {
     o[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// Self-test of the bounded wait: one CTA waits on an mbarrier that nothing
+// ever arrives at, with a short limit, exactly as the scan kernels wait on
+// their pipelines; the wait gives up, sets the status word and the kernel
+// returns, leaving the context usable.
+__global__ void selftest_wait_kernel(uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  mbar_wait(&bar, 0u, &abort_flag, limit_ns);
+}
+
 }  // namespace
+
+cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st) {
+  selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns);
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // host side

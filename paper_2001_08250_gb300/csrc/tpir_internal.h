@@ -113,6 +113,7 @@ cudaError_t launch_bloom_union(const uint64_t* deltas, uint32_t window, uint64_t
                                uint64_t* out, cudaStream_t st);
 
 int read_device_status_and_clear(int* status);
+cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
 
 // Host cuckoo metadata (cuckoo.cpp): same placement rules as the paper's
 // Section 5.3 insertion; emits the device moves of one insertion.

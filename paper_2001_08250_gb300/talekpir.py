@@ -90,6 +90,7 @@ _SIGS = [
     ("tpir_read_multi_graph_create", ctypes.c_int, [_vp, _u32, _vp]),
     ("tpir_graph_launch", ctypes.c_int, [_vp, _vp]),
     ("tpir_graph_destroy", None, [_vp]),
+    ("tpir_selftest_wait_timeout", ctypes.c_int, [_u32]),
     ("tpir_device_status", ctypes.c_int, []),
     ("tpir_bloom_create", ctypes.c_int, [_vp, _u64, _u32, _u32, _u32]),
     ("tpir_bloom_insert", ctypes.c_int, [_vp, _vp]),

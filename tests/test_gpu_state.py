@@ -218,3 +218,21 @@ def test_serve_budget_and_backpressure():
     assert st.rejected == rcs.count(talekpir.EAGAIN)
     assert st.reads_done == rcs.count(talekpir.OK)
     srv.close()
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """Failure detection without a GPU fault: a kernel waits on a barrier that
+    nothing arrives at; the bounded wait gives up after 20 ms, the status word
+    reports TPIR_ETIMEDOUT, and the context keeps serving exact reads."""
+    require_cuda()
+    t0 = time.perf_counter()
+    assert talekpir.lib().tpir_selftest_wait_timeout(20000) == talekpir.ETIMEDOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert talekpir.device_status() == talekpir.OK          # the word was cleared
+    n, d, z = 300, 2, 64
+    T = synth.table_bytes(n, d, z, seed=70)
+    R = synth.random_bits(9, n, seed=71)
+    with talekpir.DB(n, d, z) as db:
+        db.load(T)
+        assert np.array_equal(db.read_batch(R), oracle.read_batch(T, n, d, z, R))
+    assert talekpir.lib().tpir_selftest_wait_timeout(0) == talekpir.EINVAL
