@@ -40,11 +40,13 @@ B_HEAD = 256
 COPIES = 4
 HBM_PEAK_FALLBACK = 6800.0
 SMS, LOP3_PER_CLK_PER_SM = 152, 64
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 bytes
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # this workload (profiles/batched_scan_kernel_paper_scale_B256.md,
 # profiles/plain_tma_kernel_paper_scale_B1.md)
 TRAFFIC_BATCHED_B256 = 136.424704e6 + 3.473152e6
 TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
+TRAFFIC_M4RM_B256 = 136.336896e6 + 3.187968e6
 
 
 def measured_peaks() -> dict:
@@ -53,6 +55,20 @@ def measured_peaks() -> dict:
         with open(p) as fh:
             return json.load(fh)
     return {}
+
+
+def smem_peak_tbs(sm_mhz: float) -> float:
+    """Shared-memory bandwidth peak: SMs x 128 B/clk x clock."""
+    return SMS * SMEM_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+
+
+def m4rm_smem_bytes(n: int, row_words: int, B: int) -> float:
+    """Shared-memory bytes the Four-Russians kernel must move per launch: per
+    group of 8 buckets and 64-word column tile, the 256 combinations written
+    once per 256/512-request tile, plus one 256-byte lookup per request."""
+    bt = 256 if B <= 256 else 512
+    groups, wtiles, btiles = (n + 7) // 8, (row_words + 63) // 64, (B + bt - 1) // bt
+    return float(groups) * wtiles * (btiles * 256 * 64 * 4 + B * 64 * 4)
 
 
 def alu_peak_tops(sm_mhz: float) -> float:
@@ -163,8 +179,9 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--legs", default="head,plain,b32,e2e,serve,cpu,multi,large",
-                    help="comma list of: head (B=256, timed headline), plain (B=1), b32, "
+    ap.add_argument("--legs", default="head,head_lop3,plain,b32,e2e,serve,cpu,multi,large",
+                    help="comma list of: head (B=256, timed headline), head_lop3 (B=256 on the "
+                         "register-tiled LOP3 kernel), plain (B=1), b32, "
                          "e2e (host buffers), serve, cpu (oracle baseline), multi (64 uneven "
                          "tables, one graph-captured launch), large (4 GiB table, B=1024); "
                          "serve_sweep (not default: tables filling a 64 GiB budget, Poisson "
@@ -285,8 +302,26 @@ def main() -> None:
     launch_ms = statistics.mean(durs)
     ops_per_launch = B_HEAD * n * (row // 4)
     sm_mhz = (ck or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    achieved_tops = ops_per_launch / (launch_ms * 1e-3) / 1e12
-    peak_tops = alu_peak_tops(sm_mhz)
+    smem_tbs = m4rm_smem_bytes(n, row // 4, B_HEAD) / (launch_ms * 1e-3) / 1e12
+    smem_peak = smem_peak_tbs(sm_mhz)
+
+    # ---- the same batches on the register-tiled LOP3 kernel (ALU-bound)
+    lop3 = None
+    if "head_lop3" in args.legs:
+        for db in dbs:
+            db.set_kernel(2)
+        lms, ldurs, _ = timed(B_HEAD, max(3, args.steps // 2), 1, with_launch_events=True)
+        for db in dbs:
+            db.set_kernel(0)
+        lms = max_over_ranks(lms)
+        l_launch = statistics.mean(ldurs)
+        l_tops = ops_per_launch / (l_launch * 1e-3) / 1e12
+        lop3 = {"reads_per_s": USERS * world / (lms * 1e-3), "ms_per_step": lms,
+                "launch_ms": l_launch,
+                "roofline": {"bound": "alu", "achieved": l_tops, "peak": alu_peak_tops(sm_mhz),
+                             "unit": "Top/s", "frac": l_tops / alu_peak_tops(sm_mhz),
+                             "traffic": TRAFFIC_BATCHED_B256, "kernel": "batched_scan_kernel",
+                             "peak_basis": f"{SMS} SMs x {LOP3_PER_CLK_PER_SM} LOP3/clk x {sm_mhz:.0f} MHz"}}
 
     # ---- legs: plain (B=1) and B=32
     legs = {}
@@ -356,7 +391,7 @@ def main() -> None:
     multi = multi_leg(talekpir, synth, torch, stream, args) if "multi" in args.legs else None
     large = large_leg(talekpir, torch, stream, args, hbm_peak) if "large" in args.legs else None
 
-    gpu_launches = args.steps * ((USERS + B_HEAD - 1) // B_HEAD) * 2
+    gpu_launches = args.steps * ((USERS + B_HEAD - 1) // B_HEAD) * 2  # zero + scan per batch
     if rank == 0:
         line = {
             "metric": "pir_reads_per_s", "value": value, "unit": "reads/s",
@@ -365,11 +400,13 @@ def main() -> None:
             "data": "synthetic", "config": workload_config(args),
             "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": ck,
-            "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops,
-                         "unit": "Top/s", "frac": achieved_tops / peak_tops,
-                         "traffic": TRAFFIC_BATCHED_B256,
-                         "kernel": "batched_scan_kernel (+ zero_outputs_kernel)",
-                         "peak_basis": f"{SMS} SMs x {LOP3_PER_CLK_PER_SM} LOP3/clk x {sm_mhz:.0f} MHz (median SM clock sampled)"},
+            "roofline": {"bound": "smem", "achieved": smem_tbs, "peak": smem_peak,
+                         "unit": "TB/s", "frac": smem_tbs / smem_peak,
+                         "traffic": TRAFFIC_M4RM_B256,
+                         "kernel": "m4rm_scan_kernel (+ m4_zero_kernel)",
+                         "peak_basis": f"{SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk shared memory x {sm_mhz:.0f} MHz (median SM clock sampled)",
+                         "lop3_equivalent_tops": ops_per_launch / (launch_ms * 1e-3) / 1e12},
+            "head_lop3": lop3,
             "roofline_plain": {"bound": "hbm", "achieved": plain_gbs, "peak": hbm_peak,
                                "unit": "GB/s", "frac": plain_gbs / hbm_peak,
                                "traffic": TRAFFIC_PLAIN_B1,
@@ -475,6 +512,10 @@ def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:
     O = torch.empty((B, d * z), dtype=torch.uint8, device="cuda")
     db.read_batch_async(R, B, O, stream)
     bms = _events_ms(torch, stream, lambda: db.read_batch_async(R, B, O, stream), 3)
+    db.set_kernel(2)
+    db.read_batch_async(R, B, O, stream)
+    lms = _events_ms(torch, stream, lambda: db.read_batch_async(R, B, O, stream), 2)
+    db.set_kernel(0)
     db.read_batch_async(R[:1], 1, O[:1], stream)
     pms = _events_ms(torch, stream, lambda: db.read_batch_async(R[:1], 1, O[:1], stream), 16)
     db.close()
@@ -482,8 +523,11 @@ def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:
     tb = n * d * z
     return {"n": n, "d": d, "msg_bytes": z, "B": B, "table_bytes": tb,
             "batched_ms": bms, "batched_reads_per_s": B / (bms * 1e-3),
-            "batched_lop3_tops": ops / (bms * 1e-3) / 1e12,
-            "batched_lop3_frac_at_2070MHz": ops / (bms * 1e-3) / 1e12 / alu_peak_tops(2070.0),
+            "batched_lop3_equivalent_tops": ops / (bms * 1e-3) / 1e12,
+            "batched_kernel": "m4rm_scan_kernel (automatic choice at B = 1024)",
+            "lop3_kernel_ms": lms, "lop3_kernel_reads_per_s": B / (lms * 1e-3),
+            "lop3_kernel_frac_at_2070MHz": ops / (lms * 1e-3) / 1e12 / alu_peak_tops(2070.0),
+            "m4rm_smem_frac_at_2070MHz": m4rm_smem_bytes(n, d * z // 4, B) / (bms * 1e-3) / 1e12 / smem_peak_tbs(2070.0),
             "plain_ms": pms, "plain_reads_per_s": 1.0 / (pms * 1e-3),
             "plain_scan_gbs": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9,
             "plain_frac_hbm": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9 / hbm_peak}

@@ -143,10 +143,13 @@ tpir_status tpir_read_batch_async(tpir_db *db, const uint64_t *d_req_bits, uint3
                                   void *d_out, void *stream);
 
 /* Force a kernel choice for tests and benchmarks: 0 = automatic (plain for
- * B <= 4, batched otherwise), 1 = plain streaming kernel (B <= 4 per launch,
+ * B <= 4, Four-Russians for B >= 176 on rows of >= 256 bytes, register-tiled
+ * batched otherwise), 1 = plain streaming kernel (B <= 4 per launch,
  * larger B is split into launches; TMA-staged where the row width allows),
  * 2 = batched register-tiled kernel, 3 = plain kernel with register
- * streaming only (the path used for row widths the TMA-staged one skips). */
+ * streaming only (the path used for row widths the TMA-staged one skips),
+ * 4 = batched Four-Russians kernel (groups of 8 buckets, 256 combinations in
+ * shared memory, one lookup per request and group). */
 tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
 
 /* Autotuner of the batched kernel's tile shape: times every admissible shape

@@ -12,6 +12,7 @@
 namespace {
 thread_local tpir_status g_last = TPIR_OK;
 constexpr uint32_t kPlainMaxB = 4;
+constexpr uint32_t kM4rmMinB = 176;
 }  // namespace
 
 namespace tpir {
@@ -144,7 +145,17 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
   if (B == 0) return TPIR_OK;
   order_after_writes(db, st);
   int kernel = db->forced_kernel;
-  if (kernel == 0) kernel = (B <= kPlainMaxB) ? 1 : 2;
+  if (kernel == 0) {
+    // plain stream for a few requests; the Four-Russians kernel once the batch
+    // amortises its per-group combination tables (measured crossover on
+    // GB300: B ~ 170 for 4 KiB rows); the register-tiled kernel in between
+    if (B <= kPlainMaxB)
+      kernel = 1;
+    else if (B >= kM4rmMinB && db->Wd >= 64)
+      kernel = 4;
+    else
+      kernel = 2;
+  }
   cudaError_t e = cudaSuccess;
   if (kernel == 1 || kernel == 3) {
     const uint32_t* T = reinterpret_cast<const uint32_t*>(db->d_table);
@@ -156,6 +167,9 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
                                                    static_cast<uint64_t>(b0) * db->row_bytes),
                        st, kernel == 3 ? -1 : 0);
     }
+  } else if (kernel == 4) {
+    e = launch_m4rm(reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, d_req,
+                    db->words64, B, reinterpret_cast<uint32_t*>(d_out), st);
   } else {
     ScanLaunch L;
     L.njobs = 1;
@@ -419,7 +433,7 @@ tpir_status tpir_db_set_policy(tpir_db* db, uint64_t capacity, uint32_t max_evic
 }
 
 tpir_status tpir_db_set_kernel(tpir_db* db, int kernel) {
-  if (!db || kernel < 0 || kernel > 3) return TPIR_EINVAL;
+  if (!db || kernel < 0 || kernel > 4) return TPIR_EINVAL;
   db->forced_kernel = kernel;
   return TPIR_OK;
 }

@@ -957,6 +957,18 @@ cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint6
   return launch_pdl(plain_scan_kernel<4, 8>, grid, dim3(256), 0, st, T4, n, U, R, words64, B, o4, rows_per_cta);
 }
 
+int* device_status_word() {
+  static int* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<int*>(p);
+  }
+  return addr[dev];
+}
+
 int read_device_status_and_clear(int* status) {
   int v = 0;
   cudaError_t e = cudaMemcpyFromSymbol(&v, g_status, sizeof(int));

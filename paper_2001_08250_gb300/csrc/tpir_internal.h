@@ -113,6 +113,12 @@ cudaError_t launch_bloom_union(const uint64_t* deltas, uint32_t window, uint64_t
                                uint64_t* out, cudaStream_t st);
 
 int read_device_status_and_clear(int* status);
+// Device address of the status word on the current device (for kernels in
+// other translation units).
+int* device_status_word();
+// Four-Russians batched read (m4rm.cu).
+cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
+                        uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st);
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
 
 // Host cuckoo metadata (cuckoo.cpp): same placement rules as the paper's

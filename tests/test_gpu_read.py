@@ -14,7 +14,7 @@ from paper_2001_08250_gb300 import synth, talekpir
 
 pytestmark = pytest.mark.gpu
 
-PLAIN, BATCHED, PLAIN_REG = 1, 2, 3
+PLAIN, BATCHED, PLAIN_REG, M4RM = 1, 2, 3, 4
 
 
 def _db(n, d, z, T):
@@ -33,7 +33,7 @@ EDGE = [
 
 
 @pytest.mark.parametrize("n,d,z,B", EDGE)
-@pytest.mark.parametrize("kernel", [PLAIN, BATCHED, PLAIN_REG])
+@pytest.mark.parametrize("kernel", [PLAIN, BATCHED, PLAIN_REG, M4RM])
 def test_edge_shapes_bit_exact(n, d, z, B, kernel):
     require_cuda()
     T = synth.table_bytes(n, d, z, seed=21, table=n * 7 + d)
@@ -56,7 +56,7 @@ def test_empty_batch_and_zero_vector():
     T = synth.table_bytes(n, d, z, seed=3)
     with _db(n, d, z, T) as db:
         assert db.read_batch(np.zeros((0, 2), dtype=np.uint64)).shape == (0, d * z)
-        for k in (PLAIN, BATCHED, PLAIN_REG):
+        for k in (PLAIN, BATCHED, PLAIN_REG, M4RM):
             db.set_kernel(k)
             assert not db.read_batch(np.zeros((6, 2), dtype=np.uint64)).any()
             # one-hot rows return exactly their bucket
@@ -85,7 +85,7 @@ def test_plain_pir_workload_cuckoo_filled_and_three_shares():
         assert np.array_equal(db.dump(), T)
         tg = synth.targets(64, n, seed=0)
         S = synth.xor_shares(n, tg, 3, seed=0).reshape(192, -1)
-        for kernel in (PLAIN, BATCHED):
+        for kernel in (PLAIN, BATCHED, M4RM):
             db.set_kernel(kernel)
             got = db.read_batch(S)
             assert np.array_equal(got, oracle.read_batch(T, n, d, z, S))
@@ -115,7 +115,7 @@ def test_paper_scale_table_batches(paper_scale, B):
         check_rows(T, n, d, z, R, Out, sorted({0, B - 1, B // 2}))
         freivalds(T, n, d, z, R, Out, trials=12, seed=B)
         # forced kernels agree with the automatic choice
-        for k in (PLAIN, BATCHED, PLAIN_REG):
+        for k in (PLAIN, BATCHED, PLAIN_REG, M4RM):
             db.set_kernel(k)
             dO2 = dev_out(B, d * z)
             db.read_batch_async(dR, B, dO2)
@@ -174,6 +174,10 @@ def test_large_table_gf2_product_sampled():
         dO1 = dev_out(4, d * z)
         db.read_batch_async(dR, 4, dO1)
         assert np.array_equal(to_host(dO1), Out[:4])
+        db.set_kernel(M4RM)
+        dO4 = dev_out(B, d * z)
+        db.read_batch_async(dR, B, dO4)
+        assert np.array_equal(to_host(dO4), Out)
     assert talekpir.device_status() == talekpir.OK
 
 
