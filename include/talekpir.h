@@ -172,9 +172,12 @@ tpir_status tpir_tune_save(const char *path);
 tpir_status tpir_tune_load(const char *path);
 tpir_status tpir_tune_clear(void);
 
-/* Many tables in ONE persistent launch (the uneven-batching workload): job i
- * reads B_i rows of d_req_bits_i against db_i into d_out_i.  Tables may differ
- * in n, d and msg_bytes.  Up to TPIR_MAX_JOBS jobs per call. */
+/* Many tables in ONE persistent launch per kernel kind (the uneven-batching
+ * workload): job i reads B_i rows of d_req_bits_i against db_i into d_out_i.
+ * Tables may differ in n, d and msg_bytes.  Jobs of >= 176 requests on rows
+ * of >= 256 bytes share one launch of the Four-Russians kernel, the others
+ * one launch of the register-tiled kernel; both claim their items
+ * dynamically.  Up to TPIR_MAX_JOBS jobs per call. */
 #define TPIR_MAX_JOBS 128
 typedef struct {
     tpir_db *db;

@@ -12,7 +12,6 @@
 namespace {
 thread_local tpir_status g_last = TPIR_OK;
 constexpr uint32_t kPlainMaxB = 4;
-constexpr uint32_t kM4rmMinB = 176;
 }  // namespace
 
 namespace tpir {
@@ -181,6 +180,7 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
     L.jobs[0] = j;
     L.total_items = j.n_bt * j.n_wt * j.n_kc;
     L.counter_slot = next_counter_slot();
+    L.dynamic = 0;
     e = launch_zero_outputs(L, st);
     if (e == cudaSuccess)
       e = launch_batched(L, static_cast<int>(std::min<uint64_t>(L.total_items, grid)), st);
@@ -263,6 +263,34 @@ tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, 
 }
 
 tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st) {
+  // large batches on rows of >= 256 bytes: persistent Four-Russians launches
+  // (512-request tiles above 256 requests, else 256); the rest: one
+  // persistent launch of the register-tiled kernel
+  std::vector<M4Request> m4, m4w;
+  std::vector<tpir_read_job> lop3;
+  for (uint32_t i = 0; i < njobs; ++i) {
+    const tpir_read_job& q = jobs[i];
+    if (!q.db || (q.B && (!q.d_req_bits || !q.d_out))) return TPIR_EINVAL;
+    if (q.B == 0) continue;
+    if ((reinterpret_cast<uintptr_t>(q.d_out) & 15) || (reinterpret_cast<uintptr_t>(q.d_req_bits) & 7))
+      return TPIR_EINVAL;
+    const M4Request r{reinterpret_cast<const uint32_t*>(q.db->d_table), q.db->n, q.db->Wd,
+                      q.d_req_bits, q.db->words64, q.B, reinterpret_cast<uint32_t*>(q.d_out)};
+    if (q.B >= kM4rmMinB && q.db->Wd >= 64)
+      (q.B > 256 ? m4w : m4).push_back(r);
+    else
+      lop3.push_back(q);
+  }
+  tpir_status s = enqueue_multi_lop3(lop3.data(), static_cast<uint32_t>(lop3.size()), st);
+  if (s == TPIR_OK && !m4w.empty())
+    s = cuda_status(launch_m4rm_multi(m4w.data(), static_cast<uint32_t>(m4w.size()), true, st));
+  if (s == TPIR_OK && !m4.empty())
+    s = cuda_status(launch_m4rm_multi(m4.data(), static_cast<uint32_t>(m4.size()), false, st));
+  return s;
+}
+
+tpir_status enqueue_multi_lop3(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st) {
+  if (njobs == 0) return TPIR_OK;
   ScanLaunch L;
   L.njobs = 0;
   const int grid = batched_grid();
@@ -310,6 +338,7 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
   }
   L.total_items = items;
   L.counter_slot = next_counter_slot();
+  L.dynamic = 1;
   cudaError_t e = launch_zero_outputs(L, st);
   if (e == cudaSuccess) e = launch_batched(L, static_cast<int>(std::min<uint32_t>(items, grid)), st);
   return cuda_status(e);

@@ -19,9 +19,12 @@
 //     combination table, the warps meet on a bounded mbarrier, then every
 //     thread adds MR requests x 16 bytes by lookup.  Lanes run along the row,
 //     so both the stores and the lookups of a warp are bank-conflict free.
-// Items are (B-tile, W-tile, k-chunk) of one table, assigned round-robin;
-// split k-chunks XOR-reduce into the output zeroed by a PDL-chained kernel.
+// Items are (job, B-tile, W-tile, k-chunk) over one or many tables, claimed
+// dynamically from a per-launch counter; split k-chunks XOR-reduce into the
+// output zeroed by a PDL-chained kernel.
 #include <algorithm>
+#include <atomic>
+#include <vector>
 
 #include "tpir_internal.h"
 
@@ -38,6 +41,10 @@ constexpr int kM4ProducerThreads = 128;
 constexpr int kCombBytes = 256 * kWT * 4;             // 64 KiB per buffer
 constexpr uint64_t kM4WaitLimitNs = 4000000000ull;
 
+constexpr uint32_t kM4MaxJobs = TPIR_MAX_JOBS;
+constexpr uint32_t kM4CounterSlots = 256;
+constexpr uint32_t kM4End = 0xFFFFFFFFu;
+
 struct M4Job {
   const uint32_t* T;
   const uint64_t* R;
@@ -47,7 +54,49 @@ struct M4Job {
   uint32_t n_bt, n_wt, n_kc;
   uint32_t kc_rows;  // multiple of 64
   uint32_t split;
+  uint32_t item_begin;
+  uint32_t pad;
 };
+
+// The launch's job table is a kernel parameter sized by NJ: one job for a
+// single-table read (small parameters), kM4MaxJobs for many tables.
+template <int NJ>
+struct M4Launch {
+  uint32_t njobs, total_items, counter_slot;
+  uint32_t dynamic;  // informational: launches with NJ > 1 claim items from the counter
+  M4Job jobs[NJ];
+};
+
+// Item counters of the dynamic schedule (one per launch, rotating), reset by
+// the zero kernel that precedes each launch.
+__device__ uint32_t g_m4_counter[kM4CounterSlots];
+
+struct M4Item {
+  uint32_t job, bt, wt;
+  uint64_t k0, k1;
+};
+
+template <int NJ>
+__device__ __forceinline__ M4Item m4_decode(const M4Launch<NJ>& L, uint32_t item) {
+  uint32_t lo = 0, hi = L.njobs - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (L.jobs[mid].item_begin <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const M4Job& J = L.jobs[lo];
+  M4Item it;
+  it.job = lo;
+  uint32_t local = item - J.item_begin;
+  it.bt = local % J.n_bt;
+  local /= J.n_bt;
+  it.wt = local % J.n_wt;
+  it.k0 = static_cast<uint64_t>(local / J.n_wt) * J.kc_rows;
+  it.k1 = min(J.n, it.k0 + J.kc_rows);
+  return it;
+}
 
 // stage = tile + one byte per request (16 * MR per B-tile) and group
 template <int MR>
@@ -134,18 +183,22 @@ __device__ __forceinline__ void red64(uint32_t* p, uint32_t lo, uint32_t hi) {
   asm volatile("red.relaxed.gpu.global.xor.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <int MR>
+template <int MR, int NJ>
 __global__ void __launch_bounds__(kM4Threads, 1)
-    m4rm_scan_kernel(const __grid_constant__ M4Job J, uint32_t total_items, int* status) {
+    m4rm_scan_kernel(const __grid_constant__ M4Launch<NJ> L, int* status) {
   constexpr int BT = 16 * MR;  // requests per B-tile (8 warps x 2 halves x MR)
   constexpr int SB = M4Layout<MR>::kStage;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + kM4Stages;
   uint64_t* grp = empty + kM4Stages;  // consumer warps meet here once per group
+  uint64_t* claim_full = grp + 1;
+  uint64_t* claim_empty = claim_full + 1;
   uint8_t* stages = smem + 256;
   uint8_t* comb = stages + kM4Stages * SB;
   __shared__ int s_abort;
+  __shared__ uint32_t s_claim;
+  __shared__ uint32_t s_hdr[kM4Stages];
 
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -155,6 +208,8 @@ __global__ void __launch_bounds__(kM4Threads, 1)
       b_init(&empty[s], 8);
     }
     b_init(grp, 8);
+    b_init(claim_full, 1);
+    b_init(claim_empty, kM4ProducerThreads);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -165,18 +220,51 @@ __global__ void __launch_bounds__(kM4Threads, 1)
   if (threadIdx.x < kM4ProducerThreads) {
     // ---------------- producer warpgroup ----------------
     asm volatile("setmaxnreg.dec.sync.aligned.u32 56;");
+    // Thread 0 claims items (jobs listed by descending cost) from the
+    // launch's counter and passes each claim to the warpgroup (claim_full),
+    // which acknowledges it (claim_empty) before the next claim is posted.
+    // The item id rides in the header of its first stage; an END header
+    // releases the consumers.
     const uint32_t ptid = threadIdx.x;
+    uint32_t* counter = &g_m4_counter[L.counter_slot];
     bool ok = true;
-    for (uint32_t item = blockIdx.x; ok && item < total_items; item += gridDim.x) {
-      uint32_t local = item;
-      const uint32_t bt = local % J.n_bt;
-      local /= J.n_bt;
-      const uint32_t wt = local % J.n_wt;
-      const uint64_t k0 = static_cast<uint64_t>(local / J.n_wt) * J.kc_rows;
-      const uint64_t k1 = min(J.n, k0 + J.kc_rows);
-      const uint32_t w0 = wt * kWT;
+    for (uint32_t r = 0; ok; ++r) {
+      uint32_t item;
+      if constexpr (NJ > 1) {
+        if (ptid == 0) {
+          bool go = true;
+          if (r == 0)
+            asm volatile("griddepcontrol.wait;" ::: "memory");  // counter reset
+          else
+            go = b_wait(claim_empty, (r - 1) & 1u, abort_flag, status);
+          if (go) {
+            s_claim = atomicAdd(counter, 1u);
+            b_arrive(claim_full);
+          }
+        }
+        if (!b_wait(claim_full, r & 1u, abort_flag, status)) break;
+        item = *reinterpret_cast<volatile uint32_t*>(&s_claim);
+        b_arrive(claim_empty);
+      } else {
+        item = blockIdx.x + r * gridDim.x;  // one job: items cost the same
+      }
+      if (item >= L.total_items) {
+        if constexpr (NJ > 1) {
+          const uint32_t s = iter % kM4Stages, ph = (iter / kM4Stages) & 1u;
+          if (b_wait(&empty[s], ph ^ 1u, abort_flag, status)) {
+            if (ptid == 0) s_hdr[s] = kM4End;
+            b_arrive(&full[s]);
+          }
+          ++iter;
+        }
+        break;
+      }
+      const M4Item it = m4_decode(L, item);
+      const M4Job& J = L.jobs[it.job];
+      const uint64_t k0 = it.k0, k1 = it.k1;
+      const uint32_t w0 = it.wt * kWT;
       const uint32_t wcount = min(static_cast<uint32_t>(kWT), J.Wd - w0);
-      const uint32_t b0 = bt * BT;
+      const uint32_t b0 = it.bt * BT;
       for (uint64_t ks = k0; ks < k1; ks += kSR, ++iter) {
         const uint32_t s = iter % kM4Stages, ph = (iter / kM4Stages) & 1u;
         if (!b_wait(&empty[s], ph ^ 1u, abort_flag, status)) {
@@ -186,11 +274,14 @@ __global__ void __launch_bounds__(kM4Threads, 1)
         uint8_t* st = stages + s * SB;
         uint8_t* bytes = st + kTileBytes;
         const uint32_t rows = static_cast<uint32_t>(k1 - ks < kSR ? k1 - ks : kSR);
+        if constexpr (NJ > 1) {
+          if (ptid == 0 && ks == k0) s_hdr[s] = item;
+        }
         if (warp == 0) {
           if (lane == 0) b_expect(&full[s], rows * wcount * 4u);
           __syncwarp();
-          for (uint32_t r = lane; r < rows; r += 32)
-            bulk(st + r * (kWT * 4), J.T + (ks + r) * J.Wd + w0, wcount * 4u, &full[s]);
+          for (uint32_t r2 = lane; r2 < rows; r2 += 32)
+            bulk(st + r2 * (kWT * 4), J.T + (ks + r2) * J.Wd + w0, wcount * 4u, &full[s]);
         }
         // each request's 64 bits for the stage -> 8 group indices (bytes);
         // bits of rows past the chunk and requests past B are zero
@@ -228,13 +319,22 @@ __global__ void __launch_bounds__(kM4Threads, 1)
   const uint32_t rq0 = (cw * 2 + (lane >> 4)) * MR;
   const uint32_t comb0 = s_u32(comb);
   uint32_t gidx = 0;  // groups processed: parity of the group barrier, comb buffer
-  for (uint32_t item = blockIdx.x; item < total_items; item += gridDim.x) {
-    uint32_t local = item;
-    const uint32_t bt = local % J.n_bt;
-    local /= J.n_bt;
-    const uint32_t wt = local % J.n_wt;
-    const uint64_t k0 = static_cast<uint64_t>(local / J.n_wt) * J.kc_rows;
-    const uint64_t k1 = min(J.n, k0 + J.kc_rows);
+  for (uint32_t r = 0;; ++r) {
+    uint32_t item;
+    if constexpr (NJ > 1) {
+      // the header of the next item's first stage names the item (or END)
+      const uint32_t s = iter % kM4Stages, ph = (iter / kM4Stages) & 1u;
+      if (!b_wait(&full[s], ph, abort_flag, status)) return;
+      item = *reinterpret_cast<volatile uint32_t*>(&s_hdr[s]);
+      if (item == kM4End) return;
+    } else {
+      item = blockIdx.x + r * gridDim.x;
+      if (item >= L.total_items) return;
+    }
+    const M4Item it = m4_decode(L, item);
+    const M4Job& J = L.jobs[it.job];
+    const uint32_t bt = it.bt, wt = it.wt;
+    const uint64_t k0 = it.k0, k1 = it.k1;
     uint4 acc[MR];
 #pragma unroll
     for (int i = 0; i < MR; ++i) acc[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -315,12 +415,20 @@ __global__ void __launch_bounds__(kM4Threads, 1)
   }
 }
 
-__global__ void m4_zero_kernel(uint4* out, uint64_t n4) {
+// Resets the launch's item counter and zeroes the outputs of its split jobs.
+// grid.y = job.
+template <int NJ>
+__global__ void m4_zero_kernel(const __grid_constant__ M4Launch<NJ> L) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) g_m4_counter[L.counter_slot] = 0u;
+  const M4Job& J = L.jobs[blockIdx.y];
+  if (!J.split) return;
+  const uint64_t n4 = static_cast<uint64_t>(J.B) * J.Wd / 4;
+  uint4* o = reinterpret_cast<uint4*>(J.out);
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
        i += (uint64_t)gridDim.x * blockDim.x)
-    out[i] = make_uint4(0u, 0u, 0u, 0u);
+    o[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 template <typename... KArgs, typename... Args>
@@ -339,34 +447,52 @@ cudaError_t m4_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
-template <int MR>
-cudaError_t launch_m4rm_t(M4Job j, int* status, cudaStream_t st) {
+uint32_t m4_next_slot() {
+  static std::atomic<uint32_t> next{0};
+  return next.fetch_add(1, std::memory_order_relaxed) % kM4CounterSlots;
+}
+
+template <int MR, int NJ>
+cudaError_t m4_prepare() {
   static bool ready = false;
-  if (!ready) {
-    // the setmaxnreg split (128 x 56 + 256 x 224) assumes 168 registers at launch
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, m4rm_scan_kernel<MR>);
-    if (e != cudaSuccess) return e;
-    if (fa.numRegs != kScanLaunchRegs) return cudaErrorInvalidConfiguration;
-    e = cudaFuncSetAttribute(m4rm_scan_kernel<MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             M4Layout<MR>::kSmem);
-    if (e != cudaSuccess) return e;
-    ready = true;
-  }
-  constexpr uint32_t BT = 16 * MR;
-  const int grid = device_sm_count();
-  j.n_bt = (j.B + BT - 1) / BT;
-  j.n_wt = (j.Wd + kWT - 1) / kWT;
-  // k-chunks (multiples of 64 rows) minimising rounds x rows over the grid
-  const uint64_t tiles = static_cast<uint64_t>(j.n_bt) * j.n_wt;
-  const uint64_t max_kc = std::max<uint64_t>(1, (j.n + kSR - 1) / kSR);
+  if (ready) return cudaSuccess;
+  // the setmaxnreg split (128 x 56 + 256 x 224) assumes 168 registers at launch
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, m4rm_scan_kernel<MR, NJ>);
+  if (e != cudaSuccess) return e;
+  if (fa.numRegs != kScanLaunchRegs) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(m4rm_scan_kernel<MR, NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           M4Layout<MR>::kSmem);
+  if (e != cudaSuccess) return e;
+  ready = true;
+  return cudaSuccess;
+}
+
+template <int MR, int NJ>
+cudaError_t m4_launch_all(M4Launch<NJ>& L, cudaStream_t st) {
+  cudaError_t e = m4_prepare<MR, NJ>();
+  if (e != cudaSuccess) return e;
+  L.counter_slot = m4_next_slot();
+  bool any = false;
+  for (uint32_t i = 0; i < L.njobs; ++i) any |= L.jobs[i].split != 0;
+  if (any || L.dynamic)
+    e = m4_launch(m4_zero_kernel<NJ>, dim3(any ? 64 : 1, L.njobs), dim3(256), 0, st, L);
+  if (e != cudaSuccess) return e;
+  const uint32_t grid = std::min<uint32_t>(L.total_items, device_sm_count());
+  return m4_launch(m4rm_scan_kernel<MR, NJ>, dim3(grid), dim3(kM4Threads), M4Layout<MR>::kSmem,
+                   st, L, device_status_word());
+}
+
+// k-chunk of one job (multiple of 64 rows) minimising rounds x rows on the grid
+uint32_t m4_plan_single(uint64_t n, uint64_t tiles, int grid) {
+  const uint64_t max_kc = std::max<uint64_t>(1, (n + kSR - 1) / kSR);
   const uint64_t hi = std::min<uint64_t>(max_kc, static_cast<uint64_t>(grid) * 4 / tiles + 2);
   double best = 1e300;
   uint64_t best_rows = kSR;
   for (uint64_t nkc = 1; nkc <= hi; ++nkc) {
-    uint64_t rows = (j.n + nkc - 1) / nkc;
+    uint64_t rows = (n + nkc - 1) / nkc;
     rows = (rows + kSR - 1) / kSR * kSR;
-    const uint64_t items = tiles * ((j.n + rows - 1) / rows);
+    const uint64_t items = tiles * ((n + rows - 1) / rows);
     const uint64_t rounds = (items + grid - 1) / grid;
     const double cost = static_cast<double>(rounds) * (static_cast<double>(rows) + 64.0) +
                         1e-6 * static_cast<double>(items);
@@ -375,28 +501,11 @@ cudaError_t launch_m4rm_t(M4Job j, int* status, cudaStream_t st) {
       best_rows = rows;
     }
   }
-  j.kc_rows = static_cast<uint32_t>(std::min<uint64_t>(best_rows, 0xFFFFFFC0ull));
-  j.n_kc = static_cast<uint32_t>((j.n + j.kc_rows - 1) / j.kc_rows);
-  j.split = j.n_kc > 1 ? 1u : 0u;
-  const uint64_t items = tiles * j.n_kc;
-  cudaError_t e = cudaSuccess;
-  if (j.split) {
-    const uint64_t n4 = static_cast<uint64_t>(j.B) * j.Wd / 4;
-    e = m4_launch(m4_zero_kernel, dim3(static_cast<uint32_t>(std::min<uint64_t>((n4 + 255) / 256, 1024))),
-                  dim3(256), 0, st, reinterpret_cast<uint4*>(j.out), n4);
-  }
-  if (e != cudaSuccess) return e;
-  return m4_launch(m4rm_scan_kernel<MR>, dim3(static_cast<uint32_t>(std::min<uint64_t>(items, grid))),
-                   dim3(kM4Threads), M4Layout<MR>::kSmem, st, j, static_cast<uint32_t>(items), status);
+  return static_cast<uint32_t>(std::min<uint64_t>(best_rows, 0xFFFFFFC0ull));
 }
 
-}  // namespace
-
-cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
-                        uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st) {
-  int* status = device_status_word();
-  if (!status) return cudaErrorInvalidSymbol;
-  if (B == 0) return cudaSuccess;
+M4Job m4_job(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R, uint32_t words64,
+             uint32_t B, uint32_t* out, uint32_t bt) {
   M4Job j{};
   j.T = T;
   j.R = R;
@@ -405,8 +514,71 @@ cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64
   j.Wd = Wd;
   j.words64 = words64;
   j.B = B;
-  if (B > 256) return launch_m4rm_t<32>(j, status, st);
-  return launch_m4rm_t<16>(j, status, st);
+  j.n_bt = (B + bt - 1) / bt;
+  j.n_wt = (Wd + kWT - 1) / kWT;
+  return j;
+}
+
+}  // namespace
+
+cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
+                        uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  if (!device_status_word()) return cudaErrorInvalidSymbol;
+  const bool wide = B > 256;
+  M4Launch<1> L;
+  L.njobs = 1;
+  M4Job j = m4_job(T, n, Wd, R, words64, B, out, wide ? 512u : 256u);
+  j.kc_rows = m4_plan_single(n, static_cast<uint64_t>(j.n_bt) * j.n_wt, device_sm_count());
+  j.n_kc = static_cast<uint32_t>((n + j.kc_rows - 1) / j.kc_rows);
+  j.split = j.n_kc > 1 ? 1u : 0u;
+  j.item_begin = 0;
+  L.jobs[0] = j;
+  L.total_items = j.n_bt * j.n_wt * j.n_kc;
+  L.dynamic = 0;  // items of one job cost the same: static assignment, no counter
+  return wide ? m4_launch_all<32, 1>(L, st) : m4_launch_all<16, 1>(L, st);
+}
+
+cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  if (count > kM4MaxJobs) return cudaErrorInvalidValue;
+  if (!device_status_word()) return cudaErrorInvalidSymbol;
+  const int grid = device_sm_count();
+  // items of about equal cost: per 64-row chunk of one request x 64-word tile
+  // the work is the same for every job, so chunks are sized on the total
+  std::vector<M4Job> js;
+  double total_rows = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const M4Request& q = reqs[i];
+    M4Job j = m4_job(q.T, q.n, q.Wd, q.R, q.words64, q.B, q.out, wide ? 512u : 256u);
+    total_rows += static_cast<double>(j.n_bt) * j.n_wt * static_cast<double>(q.n);
+    js.push_back(j);
+  }
+  uint64_t target = static_cast<uint64_t>(total_rows / (static_cast<double>(grid) * 8.0));
+  target = std::max<uint64_t>(kSR, (target + kSR - 1) / kSR * kSR);
+  std::vector<double> cost(js.size());
+  for (size_t i = 0; i < js.size(); ++i) {
+    M4Job& j = js[i];
+    j.kc_rows = static_cast<uint32_t>(std::min<uint64_t>(target, (j.n + kSR - 1) / kSR * kSR));
+    j.n_kc = static_cast<uint32_t>((j.n + j.kc_rows - 1) / j.kc_rows);
+    j.split = j.n_kc > 1 ? 1u : 0u;
+    cost[i] = static_cast<double>(std::min<uint64_t>(j.kc_rows, j.n));
+  }
+  std::vector<size_t> order(js.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+  M4Launch<kM4MaxJobs> L;
+  L.njobs = 0;
+  uint32_t items = 0;
+  for (size_t oi : order) {
+    M4Job j = js[oi];
+    j.item_begin = items;
+    items += j.n_bt * j.n_wt * j.n_kc;
+    L.jobs[L.njobs++] = j;
+  }
+  L.total_items = items;
+  L.dynamic = 1;
+  return wide ? m4_launch_all<32, kM4MaxJobs>(L, st) : m4_launch_all<16, kM4MaxJobs>(L, st);
 }
 
 }  // namespace tpir

@@ -105,6 +105,7 @@ tpir_status tpir_autotune(tpir_db* db, uint32_t B, uint32_t reps, tpir_tune_resu
     if (!finalize_job(j)) continue;
     L.jobs[0] = j;
     L.total_items = j.n_bt * j.n_wt * j.n_kc;
+    L.dynamic = 0;
     auto run = [&]() {
       L.counter_slot = next_counter_slot();
       cudaError_t x = launch_zero_outputs(L, st);

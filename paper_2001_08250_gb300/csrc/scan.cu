@@ -584,20 +584,25 @@ __global__ void __launch_bounds__(kScanThreads, 1)
     uint32_t* counter = &g_item_counter[L.counter_slot];
     bool ok = true;
     for (uint32_t r = 0; ok; ++r) {
-      if (ptid == 0) {
-        bool go = true;
-        if (r == 0)
-          pdl_wait();  // the previous kernel reset the counter
-        else
-          go = mbar_wait(claim_empty, (r - 1) & 1u, abort_flag);
-        if (go) {
-          s_claim = atomicAdd(counter, 1u);
-          mbar_arrive(claim_full);
+      uint32_t item;
+      if (L.dynamic) {
+        if (ptid == 0) {
+          bool go = true;
+          if (r == 0)
+            pdl_wait();  // the previous kernel reset the counter
+          else
+            go = mbar_wait(claim_empty, (r - 1) & 1u, abort_flag);
+          if (go) {
+            s_claim = atomicAdd(counter, 1u);
+            mbar_arrive(claim_full);
+          }
         }
+        if (!mbar_wait(claim_full, r & 1u, abort_flag)) break;
+        item = *reinterpret_cast<volatile uint32_t*>(&s_claim);
+        mbar_arrive(claim_empty);
+      } else {
+        item = blockIdx.x + r * gridDim.x;  // items of one job cost the same
       }
-      if (!mbar_wait(claim_full, r & 1u, abort_flag)) break;
-      const uint32_t item = *reinterpret_cast<volatile uint32_t*>(&s_claim);
-      mbar_arrive(claim_empty);
       if (item >= L.total_items) {
         const uint32_t s = iter % kStages, ph = (iter / kStages) & 1u;
         if (mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {

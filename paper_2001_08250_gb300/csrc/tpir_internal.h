@@ -21,12 +21,12 @@ constexpr int kProducerThreads = 128;                // 1 warpgroup: TMA issue +
 constexpr int kScanThreads = kProducerThreads + 32 * kConsumerWarps;  // 384
 // Register split (setmaxnreg): the CTA is launched with 384 x 168 registers;
 // the producer warpgroup gives registers back, the consumers take them:
-// 128 x 56 + 256 x 224 = 64512 = 384 x 168 (an exact fit).  The launch is
+// 128 x 64 + 256 x 216 = 63488 <= 384 x 168 = 64512.  The launch is
 // refused unless the kernel was compiled to exactly kScanLaunchRegs registers
 // per thread.
 constexpr int kScanLaunchRegs = 168;
-constexpr int kProducerRegs = 56;
-constexpr int kConsumerRegs = 224;
+constexpr int kProducerRegs = 64;
+constexpr int kConsumerRegs = 216;
 static_assert(kProducerThreads * kProducerRegs + 32 * kConsumerWarps * kConsumerRegs <=
                   kScanThreads * kScanLaunchRegs,
               "register split exceeds the launch allocation");
@@ -74,7 +74,7 @@ struct ScanLaunch {
   uint32_t njobs;
   uint32_t total_items;
   uint32_t counter_slot;  // this launch's item counter (reset by the zero kernel)
-  uint32_t pad;
+  uint32_t dynamic;       // claim items from the counter (else CTA c takes c, c + grid, ...)
   ScanJob jobs[TPIR_MAX_JOBS];
 };
 // Assigns the next item-counter slot (rotating).
@@ -116,9 +116,21 @@ int read_device_status_and_clear(int* status);
 // Device address of the status word on the current device (for kernels in
 // other translation units).
 int* device_status_word();
-// Four-Russians batched read (m4rm.cu).
+// Four-Russians batched read (m4rm.cu): one table, or many in one launch.
+struct M4Request {
+  const uint32_t* T;
+  uint64_t n;
+  uint32_t Wd;
+  const uint64_t* R;
+  uint32_t words64;
+  uint32_t B;
+  uint32_t* out;
+};
 cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
                         uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st);
+// wide: 512-request tiles (jobs of more than 256 requests), else 256
+cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, cudaStream_t st);
+constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel wins
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
 
 // Host cuckoo metadata (cuckoo.cpp): same placement rules as the paper's
@@ -218,8 +230,10 @@ tpir_status apply_writes_core(tpir_db* db, uint32_t count, const uint64_t* b1, c
 // Bloom positions of `count` writes, same staging contract.
 tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, cudaStream_t st,
                               tpir_write_staging& stg);
-// Many jobs in one persistent launch (no cross-stream ordering done here).
+// Many jobs in one persistent launch per kernel kind (Four-Russians for large
+// batches, register-tiled for the rest); no cross-stream ordering done here.
 tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st);
+tpir_status enqueue_multi_lop3(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st);
 void order_writes_after_reads(tpir_db* db, cudaStream_t st);
 bool grow_dev(void** p, uint64_t* cap, uint64_t need);
 bool grow_pinned(void** p, uint64_t* cap, uint64_t need);

@@ -234,3 +234,33 @@ def test_autotuned_shape_stays_bit_exact():
         db.set_kernel(BATCHED)
         assert np.array_equal(db.read_batch(R), oracle.read_batch(T, n, d, z, R))
     talekpir.tune_clear()
+
+
+def test_multi_table_large_batches_four_russians_bit_exact():
+    """Many tables with large batches: those on rows of >= 256 bytes share one
+    persistent Four-Russians launch (B-tiles of 256), the narrow one goes to
+    the register-tiled kernel; all bit-exact."""
+    require_cuda()
+    shapes = [(1100, 2, 256, 200), (3000, 4, 1024, 256), (513, 8, 4096, 400), (700, 1, 64, 180),
+              (2049, 2, 512, 333)]
+    dbs, jobs, exp = [], [], []
+    for i, (n, d, z, B) in enumerate(shapes):
+        T = synth.table_bytes(n, d, z, seed=80, table=i)
+        R = synth.random_bits(B, n, seed=81, table=i)
+        db = _db(n, d, z, T)
+        dbs.append(db)
+        jobs.append((db, B, to_dev(R), dev_out(B, d * z)))
+        exp.append(oracle.read_batch(T, n, d, z, R))
+    talekpir.read_multi_async(jobs)
+    for (db, B, dR, dO), e in zip(jobs, exp):
+        assert np.array_equal(to_host(dO), e)
+    g = talekpir.MultiGraph(jobs)
+    for (_, _, _, dO) in jobs:
+        dO.zero_()
+    g.launch()
+    for (db, B, dR, dO), e in zip(jobs, exp):
+        assert np.array_equal(to_host(dO), e)
+    g.close()
+    for db in dbs:
+        db.close()
+    assert talekpir.device_status() == talekpir.OK
