@@ -447,8 +447,10 @@ def _events_ms(torch, stream, fn, reps):
 
 def multi_leg(talekpir, synth, torch, stream, args) -> dict:
     """64 uneven tables (n = 2^U(10,17) buckets, d in {2,4,8}, messages of
-    256/1024/4096 bytes, 16..512 reads each): all reads in ONE graph-captured
-    persistent launch, against 64 separate launches of the same kernel."""
+    256/1024/4096 bytes, 16..512 reads each): all reads in one captured graph
+    holding one persistent launch per kernel kind (batched LOP3 for the small
+    batches, Four-Russians for the large ones), against 64 separate launches
+    each taking the automatic kernel choice."""
     shapes = synth.multi_table_shapes(64, seed=3)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(3)
@@ -489,14 +491,14 @@ def multi_leg(talekpir, synth, torch, stream, args) -> dict:
     g.close()
     for db in dbs:
         db.close()
-    peak = alu_peak_tops(2070.0)
     return {"tables": len(shapes), "table_bytes": total_bytes, "reads": reads,
             "tuned_classes": tuned,
             "graph_ms": graph_ms, "separate_ms": sep_ms,
             "reads_per_s_graph": reads / (graph_ms * 1e-3),
             "reads_per_s_separate": reads / (sep_ms * 1e-3),
-            "lop3_tops_graph": ops / (graph_ms * 1e-3) / 1e12,
-            "lop3_frac_graph_at_2070MHz": ops / (graph_ms * 1e-3) / 1e12 / peak}
+            # 32-bit XOR-AND operations of the plain product per second; the
+            # Four-Russians jobs do fewer, so this can pass the LOP3 peak
+            "lop3_equivalent_tops_graph": ops / (graph_ms * 1e-3) / 1e12}
 
 
 def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:

@@ -53,6 +53,12 @@ def lib():
         L.oracle_reconstruct.restype = None
         L.oracle_splitmix64_next.argtypes = [_u64p]
         L.oracle_splitmix64_next.restype = _u64
+        L.oracle_chacha20_block.argtypes = [_vp, _u32, _vp, _vp]
+        L.oracle_chacha20_block.restype = None
+        L.oracle_mask.argtypes = [_vp, _u64, _vp]
+        L.oracle_mask.restype = None
+        L.oracle_read_batch_masked.argtypes = [_vp, _u64, _u32, _u32, _vp, _u32, _vp, _vp]
+        L.oracle_read_batch_masked.restype = None
         L.oracle_cuckoo_create.argtypes = [_u64, _u32, _u32, _u64, _u32, _u64]
         L.oracle_cuckoo_create.restype = _vp
         L.oracle_cuckoo_destroy.argtypes = [_vp]
@@ -110,6 +116,38 @@ def reconstruct(replies: np.ndarray) -> np.ndarray:
     l, nbytes = replies.shape
     out = np.empty(nbytes, dtype=np.uint8)
     lib().oracle_reconstruct(_ptr(replies), l, nbytes, _ptr(out))
+    return out
+
+
+def chacha20_block(key: bytes, counter: int, nonce: bytes) -> bytes:
+    """RFC 8439 ChaCha20 block function: 64 keystream bytes."""
+    assert len(key) == 32 and len(nonce) == 12
+    k = np.frombuffer(key, dtype=np.uint8).copy()
+    nn = np.frombuffer(nonce, dtype=np.uint8).copy()
+    out = np.empty(64, dtype=np.uint8)
+    lib().oracle_chacha20_block(_ptr(k), counter, _ptr(nn), _ptr(out))
+    return out.tobytes()
+
+
+def mask(seed, nbytes: int) -> np.ndarray:
+    """One-time mask P = PRNG(p) of Section 6 (ChaCha20 keystream, zero nonce)."""
+    s = np.ascontiguousarray(np.frombuffer(bytes(seed), dtype=np.uint8) if isinstance(seed, (bytes, bytearray))
+                             else seed, dtype=np.uint8)
+    assert s.size == 32
+    out = np.empty(nbytes, dtype=np.uint8)
+    lib().oracle_mask(_ptr(s), nbytes, _ptr(out))
+    return out
+
+
+def read_batch_masked(T: np.ndarray, n: int, d: int, z: int, R: np.ndarray,
+                      seeds: np.ndarray) -> np.ndarray:
+    """Masked responses R_b XOR PRNG(p_b) of Section 6 step 7."""
+    T = np.ascontiguousarray(T, dtype=np.uint8)
+    R = np.ascontiguousarray(R, dtype=np.uint64).reshape(-1, (n + 63) // 64)
+    B = R.shape[0]
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint8).reshape(B, 32)
+    out = np.empty((B, d * z), dtype=np.uint8)
+    lib().oracle_read_batch_masked(_ptr(T), n, d, z, _ptr(R), B, _ptr(seeds), _ptr(out))
     return out
 
 

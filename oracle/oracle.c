@@ -7,6 +7,9 @@
  *
  *   oracle_read           Section 2, step 5 (server answer of Chor et al.'s IT-PIR)
  *   oracle_reconstruct    Section 2, step 6 (client XOR of the l replies)
+ *   oracle_mask           Section 6, step 6 (one-time mask PRNG(p); ChaCha20
+ *                         of RFC 8439 taken as the PRNG)
+ *   oracle_read_batch_masked  Section 6, step 7 (masked response R XOR P)
  *   oracle_cuckoo_insert  Section 5.3 (blocked cuckoo insertion, FIFO collection)
  *   oracle_bloom_*        Section 7 (interest vectors, global interest vector,
  *                         window of deltas)
@@ -55,6 +58,82 @@ uint64_t oracle_splitmix64_next(uint64_t *state) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Serialized PIR: one-time masks                                            */
+/* ------------------------------------------------------------------------ */
+
+static uint32_t rotl32(uint32_t v, int c) { return (v << c) | (v >> (32 - c)); }
+
+static uint32_t load_le32(const uint8_t *p) {
+    return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+/* RFC 8439 section 2.1: the quarter round on four words of the state. */
+static void quarter_round(uint32_t *x, int a, int b, int c, int d) {
+    x[a] += x[b]; x[d] ^= x[a]; x[d] = rotl32(x[d], 16);
+    x[c] += x[d]; x[b] ^= x[c]; x[b] = rotl32(x[b], 12);
+    x[a] += x[b]; x[d] ^= x[a]; x[d] = rotl32(x[d], 8);
+    x[c] += x[d]; x[b] ^= x[c]; x[b] = rotl32(x[b], 7);
+}
+
+void oracle_chacha20_block(const uint8_t key[32], uint32_t counter, const uint8_t nonce[12],
+                           uint8_t out[64]) {
+    /* RFC 8439 section 2.3: state = the four words of "expand 32-byte k",
+     * the key, the block counter, the nonce (all little-endian words) */
+    uint32_t state[16], x[16];
+    state[0] = load_le32((const uint8_t *)"expa");
+    state[1] = load_le32((const uint8_t *)"nd 3");
+    state[2] = load_le32((const uint8_t *)"2-by");
+    state[3] = load_le32((const uint8_t *)"te k");
+    for (int i = 0; i < 8; i++) state[4 + i] = load_le32(key + 4 * i);
+    state[12] = counter;
+    for (int i = 0; i < 3; i++) state[13 + i] = load_le32(nonce + 4 * i);
+    for (int i = 0; i < 16; i++) x[i] = state[i];
+    /* 20 rounds: ten times a column round then a diagonal round */
+    for (int r = 0; r < 10; r++) {
+        quarter_round(x, 0, 4, 8, 12);
+        quarter_round(x, 1, 5, 9, 13);
+        quarter_round(x, 2, 6, 10, 14);
+        quarter_round(x, 3, 7, 11, 15);
+        quarter_round(x, 0, 5, 10, 15);
+        quarter_round(x, 1, 6, 11, 12);
+        quarter_round(x, 2, 7, 8, 13);
+        quarter_round(x, 3, 4, 9, 14);
+    }
+    /* add the input state, serialise little-endian */
+    for (int i = 0; i < 16; i++) {
+        uint32_t v = x[i] + state[i];
+        out[4 * i + 0] = (uint8_t)(v & 0xFF);
+        out[4 * i + 1] = (uint8_t)((v >> 8) & 0xFF);
+        out[4 * i + 2] = (uint8_t)((v >> 16) & 0xFF);
+        out[4 * i + 3] = (uint8_t)((v >> 24) & 0xFF);
+    }
+}
+
+void oracle_mask(const uint8_t seed[32], uint64_t nbytes, uint8_t *out) {
+    const uint8_t nonce[12] = {0};
+    uint8_t block[64];
+    for (uint64_t off = 0; off < nbytes; off += 64) {
+        oracle_chacha20_block(seed, (uint32_t)(off / 64), nonce, block);
+        for (uint64_t j = 0; j < 64 && off + j < nbytes; j++) out[off + j] = block[j];
+    }
+}
+
+void oracle_read_batch_masked(const uint8_t *T, uint64_t n, uint32_t d, uint32_t z,
+                              const uint64_t *R, uint32_t B, const uint8_t *seeds, uint8_t *out) {
+    uint64_t words = (n + 63) / 64;
+    uint64_t bucket = (uint64_t)d * z;
+    uint8_t *mask = (uint8_t *)malloc(bucket ? bucket : 1);
+    if (!mask) return;
+    for (uint32_t b = 0; b < B; b++) {
+        uint8_t *o = out + (uint64_t)b * bucket;
+        oracle_read(T, n, d, z, R + (uint64_t)b * words, o);   /* R_i, step 5 */
+        oracle_mask(seeds + (uint64_t)b * 32, bucket, mask);  /* P_i, step 6 */
+        for (uint64_t j = 0; j < bucket; j++) o[j] ^= mask[j];  /* R_i XOR P_i, step 7 */
+    }
+    free(mask);
 }
 
 /* ------------------------------------------------------------------------ */

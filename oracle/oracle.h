@@ -44,6 +44,23 @@ void oracle_reconstruct(const uint8_t *replies, uint32_t l, uint64_t bytes, uint
  * and returns the next output. */
 uint64_t oracle_splitmix64_next(uint64_t *state);
 
+/* ---- Serialized PIR (Section 6) ---------------------------------------- */
+
+/* The ChaCha20 block function as RFC 8439 section 2.3 defines it: the 64
+ * keystream bytes of block `counter` under a 32-byte key and a 12-byte nonce. */
+void oracle_chacha20_block(const uint8_t key[32], uint32_t counter, const uint8_t nonce[12],
+                           uint8_t out[64]);
+
+/* One-time mask of Section 6 step 6, P = PRNG(p): the paper leaves the PRNG
+ * open; here it is the ChaCha20 keystream under key p (32 bytes) with an
+ * all-zero nonce, blocks 0, 1, 2, ... in order, cut to nbytes bytes. */
+void oracle_mask(const uint8_t seed[32], uint64_t nbytes, uint8_t *out);
+
+/* Masked server responses, Section 6 step 7: out[b] = oracle_read(R[b]) XOR
+ * PRNG(seeds[b]); seeds has B rows of 32 bytes. */
+void oracle_read_batch_masked(const uint8_t *T, uint64_t n, uint32_t d, uint32_t z,
+                              const uint64_t *R, uint32_t B, const uint8_t *seeds, uint8_t *out);
+
 /* ---- blocked cuckoo table with FIFO garbage collection (Section 5.3) --- */
 
 typedef struct oracle_cuckoo oracle_cuckoo;

@@ -43,6 +43,7 @@ P_BLOOM = 7
 P_ARRIVAL = 8
 P_SHAPES = 9
 P_MIX = 10
+P_SEED = 11
 
 # fixed hash salts used to turn a 64-bit write key into its two buckets and
 # its Bloom positions (stand-ins for the client's PRF and cryptographic hashes)
@@ -166,6 +167,13 @@ def xor_shares(n: int, tgts: np.ndarray, l: int, seed: int, table: int = 0) -> n
         last ^= r[:, j, :]
     out[:, l - 1, :] = last
     return out
+
+
+def mask_seeds(count: int, seed: int, table: int = 0, server: int = 0) -> np.ndarray:
+    """``count`` client seeds p of 32 uniform random bytes each (Section 6
+    step 2), one stream per (table, server); uint8 [count, 32]."""
+    w = stream(stream_key(seed, table, P_SEED, server), count * 4)
+    return w.view(np.uint8).reshape(count, 32).copy()
 
 
 # --------------------------------------------------------------------------
