@@ -142,6 +142,32 @@ tpir_status tpir_read_batch(tpir_db *db, const uint64_t *req_bits, uint32_t B, v
 tpir_status tpir_read_batch_async(tpir_db *db, const uint64_t *d_req_bits, uint32_t B,
                                   void *d_out, void *stream);
 
+/* ---- Serialized PIR (Section 6) -----------------------------------------
+ * Masked reads, steps 5-7: reply b = (XOR of the buckets request b selects)
+ * XOR P_b, with P_b = PRNG(seed_b) the one-time mask of the 32-byte seed the
+ * client sent with the request.  The paper leaves the PRNG open; here it is
+ * the ChaCha20 keystream of RFC 8439 under key seed_b with an all-zero nonce,
+ * blocks 0, 1, 2, ... in order, cut to row_bytes.  seeds: B rows of 32 bytes.
+ * Same kernels, ordering and error behaviour as the unmasked reads; the masks
+ * are generated on the device by the kernel that initialises the replies.
+ * Synchronous form: all buffers are host memory. */
+tpir_status tpir_read_batch_masked(tpir_db *db, const uint64_t *req_bits, uint32_t B,
+                                   const uint8_t *seeds, void *out);
+/* Asynchronous form: device buffers; d_seeds 16-byte aligned (else EINVAL). */
+tpir_status tpir_read_batch_masked_async(tpir_db *db, const uint64_t *d_req_bits, uint32_t B,
+                                         const uint8_t *d_seeds, void *d_out, void *stream);
+/* The masks alone, P_b for b < rows, nbytes each (a multiple of 16), into the
+ * device buffer d_out (rows x nbytes): the client's step 9, or a leader that
+ * checks a combination.  d_seeds and d_out 16-byte aligned. */
+tpir_status tpir_mask_generate(const uint8_t *d_seeds, uint32_t rows, uint64_t nbytes,
+                               void *d_out, void *stream);
+/* The leader's combination, step 8: d_dst = XOR of `count` device buffers
+ * d_srcs[0..count-1] of nbytes each (nbytes a multiple of 16, every buffer
+ * 16-byte aligned; d_dst may be one of the sources; 1 <= count <= 64).
+ * d_srcs itself is a host array of device pointers. */
+tpir_status tpir_xor_combine(const void *const *d_srcs, uint32_t count, uint64_t nbytes,
+                             void *d_dst, void *stream);
+
 /* Force a kernel choice for tests and benchmarks: 0 = automatic (plain for
  * B <= 4, Four-Russians for B >= 176 on rows of >= 256 bytes, register-tiled
  * batched otherwise), 1 = plain streaming kernel (B <= 4 per launch,
@@ -175,21 +201,25 @@ tpir_status tpir_tune_clear(void);
 /* Many tables in ONE persistent launch per kernel kind (the uneven-batching
  * workload): job i reads B_i rows of d_req_bits_i against db_i into d_out_i.
  * Tables may differ in n, d and msg_bytes.  Jobs of >= 176 requests on rows
- * of >= 256 bytes share one launch of the Four-Russians kernel, the others
- * one launch of the register-tiled kernel; both claim their items
- * dynamically.  Up to TPIR_MAX_JOBS jobs per call. */
+ * of >= 256 bytes go to the Four-Russians kernel (one launch for jobs of up
+ * to 256 requests, one for larger ones), the others to one launch of the
+ * register-tiled kernel; every launch claims its items dynamically.  A job
+ * with d_seeds (B x 32 bytes, 16-byte aligned) is masked as in
+ * tpir_read_batch_masked_async; NULL = plain replies.  Up to TPIR_MAX_JOBS
+ * jobs per call. */
 #define TPIR_MAX_JOBS 128
 typedef struct {
     tpir_db *db;
     uint32_t B;
     const uint64_t *d_req_bits;
     void *d_out;
+    const uint8_t *d_seeds;
 } tpir_read_job;
 tpir_status tpir_read_multi_async(const tpir_read_job *jobs, uint32_t njobs, void *stream);
 
-/* The same many-table read captured once into a CUDA graph (one zero kernel
- * and one persistent scan kernel), for workloads that repeat the launch with
- * the same buffers.  tpir_graph_launch orders the replay after every write
+/* The same many-table read captured once into a CUDA graph (per kernel kind
+ * one output-initialisation kernel and one persistent scan kernel), for
+ * workloads that repeat the launch with the same buffers.  tpir_graph_launch orders the replay after every write
  * already made to the jobs' dbs.  The dbs and buffers must outlive the graph. */
 typedef struct tpir_graph tpir_graph;
 tpir_status tpir_read_multi_graph_create(const tpir_read_job *jobs, uint32_t njobs,

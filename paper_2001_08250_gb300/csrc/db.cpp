@@ -140,7 +140,7 @@ uint32_t next_counter_slot() {
 }
 
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
-                         cudaStream_t st) {
+                         cudaStream_t st, const uint8_t* d_seeds) {
   if (B == 0) return TPIR_OK;
   order_after_writes(db, st);
   int kernel = db->forced_kernel;
@@ -164,15 +164,17 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
                        db->words64, nb,
                        reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(d_out) +
                                                    static_cast<uint64_t>(b0) * db->row_bytes),
-                       st, kernel == 3 ? -1 : 0);
+                       d_seeds ? d_seeds + static_cast<uint64_t>(b0) * 32 : nullptr, st,
+                       kernel == 3 ? -1 : 0);
     }
   } else if (kernel == 4) {
     e = launch_m4rm(reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, d_req,
-                    db->words64, B, reinterpret_cast<uint32_t*>(d_out), st);
+                    db->words64, B, reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
   } else {
     ScanLaunch L;
     L.njobs = 1;
     ScanJob j = make_job(db, d_req, B, d_out);
+    j.seeds = d_seeds;
     const int grid = batched_grid();
     plan_single(j, grid);
     j.item_begin = 0;
@@ -272,10 +274,12 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
     const tpir_read_job& q = jobs[i];
     if (!q.db || (q.B && (!q.d_req_bits || !q.d_out))) return TPIR_EINVAL;
     if (q.B == 0) continue;
-    if ((reinterpret_cast<uintptr_t>(q.d_out) & 15) || (reinterpret_cast<uintptr_t>(q.d_req_bits) & 7))
+    if ((reinterpret_cast<uintptr_t>(q.d_out) & 15) || (reinterpret_cast<uintptr_t>(q.d_req_bits) & 7) ||
+        (reinterpret_cast<uintptr_t>(q.d_seeds) & 15))
       return TPIR_EINVAL;
     const M4Request r{reinterpret_cast<const uint32_t*>(q.db->d_table), q.db->n, q.db->Wd,
-                      q.d_req_bits, q.db->words64, q.B, reinterpret_cast<uint32_t*>(q.d_out)};
+                      q.d_req_bits, q.db->words64, q.B, reinterpret_cast<uint32_t*>(q.d_out),
+                      static_cast<const uint8_t*>(q.d_seeds)};
     if (q.B >= kM4rmMinB && q.db->Wd >= 64)
       (q.B > 256 ? m4w : m4).push_back(r);
     else
@@ -301,9 +305,11 @@ tpir_status enqueue_multi_lop3(const tpir_read_job* jobs, uint32_t njobs, cudaSt
     const tpir_read_job& q = jobs[i];
     if (!q.db || (q.B && (!q.d_req_bits || !q.d_out))) return TPIR_EINVAL;
     if (q.B == 0) continue;
-    if ((reinterpret_cast<uintptr_t>(q.d_out) & 15) || (reinterpret_cast<uintptr_t>(q.d_req_bits) & 7))
+    if ((reinterpret_cast<uintptr_t>(q.d_out) & 15) || (reinterpret_cast<uintptr_t>(q.d_req_bits) & 7) ||
+        (reinterpret_cast<uintptr_t>(q.d_seeds) & 15))
       return TPIR_EINVAL;
     ScanJob j = make_job(q.db, q.d_req_bits, q.B, q.d_out);
+    j.seeds = static_cast<const uint8_t*>(q.d_seeds);
     const double tiles = static_cast<double>((j.B + j.shape.bt() - 1) / j.shape.bt()) *
                          ((j.Wd + j.shape.wt() - 1) / j.shape.wt());
     total += tiles * static_cast<double>(j.n) * row_cost(j);
@@ -524,18 +530,27 @@ tpir_status tpir_write_batch(tpir_db* db, uint32_t count, const uint64_t* b1, co
                            evictions_out, db->stream, db->stage);
 }
 
-tpir_status tpir_read_batch(tpir_db* db, const uint64_t* req_bits, uint32_t B, void* out) {
+// Synchronous read through the db's own staging; seeds (host, B x 32 bytes)
+// masks the replies, null = plain.
+static tpir_status read_batch_sync(tpir_db* db, const uint64_t* req_bits, uint32_t B,
+                                   const uint8_t* seeds, void* out) {
   if (!db) return TPIR_EINVAL;
   if (B == 0) return TPIR_OK;
   if (!req_bits || !out) return TPIR_EINVAL;
   const uint64_t rb = static_cast<uint64_t>(B) * db->words64 * 8;
   const uint64_t ob = static_cast<uint64_t>(B) * db->row_bytes;
-  if (!grow_dev(reinterpret_cast<void**>(&db->d_req), &db->req_cap, rb) ||
+  // the seeds follow the request rows in the same staging buffer, 16-byte aligned
+  const uint64_t ra = (rb + 15) / 16 * 16;
+  const uint64_t sb = seeds ? static_cast<uint64_t>(B) * 32 : 0;
+  if (!grow_dev(reinterpret_cast<void**>(&db->d_req), &db->req_cap, ra + sb) ||
       !grow_dev(reinterpret_cast<void**>(&db->d_out), &db->out_cap, ob))
     return TPIR_ENOMEM;
+  uint8_t* d_seeds = seeds ? reinterpret_cast<uint8_t*>(db->d_req) + ra : nullptr;
   cudaError_t e = cudaMemcpyAsync(db->d_req, req_bits, rb, cudaMemcpyHostToDevice, db->stream);
+  if (e == cudaSuccess && seeds)
+    e = cudaMemcpyAsync(d_seeds, seeds, sb, cudaMemcpyHostToDevice, db->stream);
   if (e != cudaSuccess) return cuda_status(e);
-  tpir_status s = enqueue_read(db, db->d_req, B, db->d_out, db->stream);
+  tpir_status s = enqueue_read(db, db->d_req, B, db->d_out, db->stream, d_seeds);
   if (s != TPIR_OK) return s;
   e = cudaMemcpyAsync(out, db->d_out, ob, cudaMemcpyDeviceToHost, db->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
@@ -543,6 +558,16 @@ tpir_status tpir_read_batch(tpir_db* db, const uint64_t* req_bits, uint32_t B, v
   int st = 0;
   if (read_device_status_and_clear(&st) != 0) return TPIR_ECUDA;
   return st ? static_cast<tpir_status>(st) : TPIR_OK;
+}
+
+tpir_status tpir_read_batch(tpir_db* db, const uint64_t* req_bits, uint32_t B, void* out) {
+  return read_batch_sync(db, req_bits, B, nullptr, out);
+}
+
+tpir_status tpir_read_batch_masked(tpir_db* db, const uint64_t* req_bits, uint32_t B,
+                                   const uint8_t* seeds, void* out) {
+  if (B && !seeds) return TPIR_EINVAL;
+  return read_batch_sync(db, req_bits, B, seeds, out);
 }
 
 tpir_status tpir_read_batch_async(tpir_db* db, const uint64_t* d_req_bits, uint32_t B,
@@ -553,6 +578,17 @@ tpir_status tpir_read_batch_async(tpir_db* db, const uint64_t* d_req_bits, uint3
   if ((reinterpret_cast<uintptr_t>(d_out) & 15) || (reinterpret_cast<uintptr_t>(d_req_bits) & 7))
     return TPIR_EINVAL;
   return enqueue_read(db, d_req_bits, B, d_out, static_cast<cudaStream_t>(stream));
+}
+
+tpir_status tpir_read_batch_masked_async(tpir_db* db, const uint64_t* d_req_bits, uint32_t B,
+                                         const uint8_t* d_seeds, void* d_out, void* stream) {
+  if (!db) return TPIR_EINVAL;
+  if (B == 0) return TPIR_OK;
+  if (!d_req_bits || !d_out || !d_seeds) return TPIR_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 15) || (reinterpret_cast<uintptr_t>(d_req_bits) & 7) ||
+      (reinterpret_cast<uintptr_t>(d_seeds) & 15))
+    return TPIR_EINVAL;
+  return enqueue_read(db, d_req_bits, B, d_out, static_cast<cudaStream_t>(stream), d_seeds);
 }
 
 tpir_status tpir_read_multi_async(const tpir_read_job* jobs, uint32_t njobs, void* stream) {

@@ -26,6 +26,7 @@
 #include <atomic>
 #include <vector>
 
+#include "chacha.cuh"
 #include "tpir_internal.h"
 
 namespace tpir {
@@ -49,6 +50,7 @@ struct M4Job {
   const uint32_t* T;
   const uint64_t* R;
   uint32_t* out;
+  const uint8_t* seeds;  // B x 32-byte mask seeds, or null
   uint64_t n;
   uint32_t Wd, words64, B;
   uint32_t n_bt, n_wt, n_kc;
@@ -415,7 +417,8 @@ __global__ void __launch_bounds__(kM4Threads, 1)
   }
 }
 
-// Resets the launch's item counter and zeroes the outputs of its split jobs.
+// Resets the launch's item counter and initialises the outputs of its split
+// jobs (zeros, or the masks of masked jobs).
 // grid.y = job.
 template <int NJ>
 __global__ void m4_zero_kernel(const __grid_constant__ M4Launch<NJ> L) {
@@ -424,11 +427,8 @@ __global__ void m4_zero_kernel(const __grid_constant__ M4Launch<NJ> L) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) g_m4_counter[L.counter_slot] = 0u;
   const M4Job& J = L.jobs[blockIdx.y];
   if (!J.split) return;
-  const uint64_t n4 = static_cast<uint64_t>(J.B) * J.Wd / 4;
-  uint4* o = reinterpret_cast<uint4*>(J.out);
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    o[i] = make_uint4(0u, 0u, 0u, 0u);
+  init_replies(reinterpret_cast<uint4*>(J.out), J.B, J.Wd / 4, J.seeds,
+               blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
 template <typename... KArgs, typename... Args>
@@ -505,11 +505,12 @@ uint32_t m4_plan_single(uint64_t n, uint64_t tiles, int grid) {
 }
 
 M4Job m4_job(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R, uint32_t words64,
-             uint32_t B, uint32_t* out, uint32_t bt) {
+             uint32_t B, uint32_t* out, const uint8_t* seeds, uint32_t bt) {
   M4Job j{};
   j.T = T;
   j.R = R;
   j.out = out;
+  j.seeds = seeds;
   j.n = n;
   j.Wd = Wd;
   j.words64 = words64;
@@ -522,16 +523,17 @@ M4Job m4_job(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R, uint
 }  // namespace
 
 cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
-                        uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st) {
+                        uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+                        cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   if (!device_status_word()) return cudaErrorInvalidSymbol;
   const bool wide = B > 256;
   M4Launch<1> L;
   L.njobs = 1;
-  M4Job j = m4_job(T, n, Wd, R, words64, B, out, wide ? 512u : 256u);
+  M4Job j = m4_job(T, n, Wd, R, words64, B, out, seeds, wide ? 512u : 256u);
   j.kc_rows = m4_plan_single(n, static_cast<uint64_t>(j.n_bt) * j.n_wt, device_sm_count());
   j.n_kc = static_cast<uint32_t>((n + j.kc_rows - 1) / j.kc_rows);
-  j.split = j.n_kc > 1 ? 1u : 0u;
+  j.split = (j.n_kc > 1 || seeds) ? 1u : 0u;  // masks: reduce onto the masked replies
   j.item_begin = 0;
   L.jobs[0] = j;
   L.total_items = j.n_bt * j.n_wt * j.n_kc;
@@ -550,7 +552,7 @@ cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, 
   double total_rows = 0;
   for (uint32_t i = 0; i < count; ++i) {
     const M4Request& q = reqs[i];
-    M4Job j = m4_job(q.T, q.n, q.Wd, q.R, q.words64, q.B, q.out, wide ? 512u : 256u);
+    M4Job j = m4_job(q.T, q.n, q.Wd, q.R, q.words64, q.B, q.out, q.seeds, wide ? 512u : 256u);
     total_rows += static_cast<double>(j.n_bt) * j.n_wt * static_cast<double>(q.n);
     js.push_back(j);
   }
@@ -561,7 +563,7 @@ cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, 
     M4Job& j = js[i];
     j.kc_rows = static_cast<uint32_t>(std::min<uint64_t>(target, (j.n + kSR - 1) / kSR * kSR));
     j.n_kc = static_cast<uint32_t>((j.n + j.kc_rows - 1) / j.kc_rows);
-    j.split = j.n_kc > 1 ? 1u : 0u;
+    j.split = (j.n_kc > 1 || j.seeds) ? 1u : 0u;
     cost[i] = static_cast<double>(std::min<uint64_t>(j.kc_rows, j.n));
   }
   std::vector<size_t> order(js.size());

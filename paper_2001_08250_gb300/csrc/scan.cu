@@ -18,6 +18,7 @@
 //                       launch serves one table or many uneven tables.
 #include <algorithm>
 
+#include "chacha.cuh"
 #include "tpir_internal.h"
 
 namespace tpir {
@@ -706,31 +707,29 @@ __global__ void __launch_bounds__(kScanThreads, 1)
   }
 }
 
-// Zeroes a reply buffer before a scan XOR-reduces into it.  It lets the scan
-// launch at once (the scan only waits for it before its reduction) but waits
-// itself for the previous kernel, which may still be reducing into a buffer
-// the caller reuses.
-__global__ void zero_u4_kernel(uint4* __restrict__ out, uint64_t n4) {
+// Initialises B replies before a scan XOR-reduces into them: zeros, or the
+// one-time masks of a serialized-PIR read.  It lets the scan launch at once
+// (the scan only waits for it before its reduction) but waits itself for the
+// previous kernel, which may still be reducing into a buffer the caller reuses.
+__global__ void init_replies_kernel(uint4* __restrict__ out, uint32_t B, uint32_t row_u4,
+                                    const uint8_t* __restrict__ seeds) {
   pdl_launch_dependents();
   pdl_wait();
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    out[i] = make_uint4(0u, 0u, 0u, 0u);
+  init_replies(out, B, row_u4, seeds, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+               (uint64_t)gridDim.x * blockDim.x);
 }
 
-// Resets the launch's item counter and zeroes the outputs of the jobs whose
-// partial replies are XOR-reduced.  grid.y = job.
+// Resets the launch's item counter and initialises the outputs of the jobs
+// whose partial replies are XOR-reduced (zeros, or the masks of a masked
+// job).  grid.y = job.
 __global__ void zero_outputs_kernel(const __grid_constant__ ScanLaunch L) {
   pdl_launch_dependents();
   pdl_wait();
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) g_item_counter[L.counter_slot] = 0u;
   const ScanJob& J = L.jobs[blockIdx.y];
   if (!J.split) return;
-  const uint64_t n4 = static_cast<uint64_t>(J.B) * J.Wd / 4;
-  uint4* o = reinterpret_cast<uint4*>(J.out);
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    o[i] = make_uint4(0u, 0u, 0u, 0u);
+  init_replies(reinterpret_cast<uint4*>(J.out), J.B, J.Wd / 4, J.seeds,
+               blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
 // Self-test of the bounded wait: one CTA waits on an mbarrier that nothing
@@ -861,7 +860,7 @@ bool finalize_job(ScanJob& j) {
   j.n_bt = (j.B + s.bt() - 1) / s.bt();
   j.n_wt = (j.Wd + s.wt() - 1) / s.wt();
   j.n_kc = static_cast<uint32_t>((j.n + j.kc_rows - 1) / j.kc_rows);
-  j.split = (j.n_kc > 1 || s.wk > 1) ? 1u : 0u;
+  j.split = (j.n_kc > 1 || s.wk > 1 || j.seeds) ? 1u : 0u;
   return true;
 }
 
@@ -929,13 +928,16 @@ static bool plain_tma_ok(uint32_t U, int nb) {
 }
 
 cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
-                         uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st, int ctas) {
+                         uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+                         cudaStream_t st, int ctas) {
   if (B == 0) return cudaSuccess;
   const uint32_t U = Wd / 4;
   uint4* o4 = reinterpret_cast<uint4*>(out);
-  const uint64_t n4 = static_cast<uint64_t>(B) * U;
-  cudaError_t e = launch_pdl(zero_u4_kernel, dim3(static_cast<uint32_t>(std::min<uint64_t>((n4 + 255) / 256, 1024))),
-                             dim3(256), 0, st, o4, n4);
+  // one thread per 16-byte word (zeros) or per 64-byte keystream block (masks)
+  const uint64_t work = seeds ? static_cast<uint64_t>(B) * ((U + 3) / 4) : static_cast<uint64_t>(B) * U;
+  cudaError_t e = launch_pdl(init_replies_kernel,
+                             dim3(static_cast<uint32_t>(std::min<uint64_t>((work + 255) / 256, 1024))),
+                             dim3(256), 0, st, o4, B, U, seeds);
   if (e != cudaSuccess) return e;
   const int nb = B == 1 ? 1 : (B == 2 ? 2 : 4);
   const uint4* T4 = reinterpret_cast<const uint4*>(T);

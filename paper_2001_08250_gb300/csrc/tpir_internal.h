@@ -55,7 +55,8 @@ struct Shape {
 struct ScanJob {
   const uint32_t* T;   // table, n rows of Wd words
   const uint64_t* R;   // request bits, B rows of words64
-  uint32_t* out;       // B rows of Wd words (zeroed first when split)
+  uint32_t* out;       // B rows of Wd words (initialised first when split)
+  const uint8_t* seeds;  // B x 32-byte mask seeds (serialized PIR), or null
   uint64_t n;
   uint32_t Wd;         // row length in 32-bit words (d*msg_bytes/4)
   uint32_t words64;    // u64 words per request row
@@ -64,7 +65,7 @@ struct ScanJob {
   uint32_t n_bt, n_wt, n_kc;
   uint32_t kc_rows;    // buckets per k-chunk (multiple of 64)
   uint32_t item_begin; // index of this job's first item in the launch
-  uint32_t split;      // partial replies are XOR-reduced (n_kc > 1 or wk > 1)
+  uint32_t split;      // partial replies are XOR-reduced (n_kc > 1, wk > 1 or masked)
 };
 
 constexpr uint32_t kItemCounterSlots = 256;  // launches with distinct item counters
@@ -77,6 +78,7 @@ struct ScanLaunch {
   uint32_t dynamic;       // claim items from the counter (else CTA c takes c, c + grid, ...)
   ScanJob jobs[TPIR_MAX_JOBS];
 };
+static_assert(sizeof(ScanLaunch) <= 32000, "kernel parameters must stay below 32 KB");
 // Assigns the next item-counter slot (rotating).
 uint32_t next_counter_slot();
 
@@ -90,8 +92,10 @@ int scan_stage_bytes(const Shape& s);
 
 // Launch helpers (scan.cu).  All return cudaError_t of the launch.
 cudaError_t launch_batched(const ScanLaunch& L, int grid, cudaStream_t st);
+// seeds: B x 32-byte mask seeds, or null (the replies start at zero)
 cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
-                         uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st, int ctas);
+                         uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+                         cudaStream_t st, int ctas);
 cudaError_t launch_zero_outputs(const ScanLaunch& L, cudaStream_t st);
 int device_sm_count();
 int plain_ctas_per_sm();
@@ -125,9 +129,18 @@ struct M4Request {
   uint32_t words64;
   uint32_t B;
   uint32_t* out;
+  const uint8_t* seeds;  // B x 32-byte mask seeds, or null
 };
 cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
-                        uint32_t words64, uint32_t B, uint32_t* out, cudaStream_t st);
+                        uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+                        cudaStream_t st);
+// Serialized-PIR helpers (mask.cu): the masks alone, and the leader's XOR of
+// several replies.
+cudaError_t launch_mask_fill(uint4* out, uint32_t rows, uint32_t row_u4, const uint8_t* seeds,
+                             cudaStream_t st);
+constexpr uint32_t kMaxCombine = 64;
+cudaError_t launch_xor_combine(const uint4* const* srcs, uint32_t count, uint64_t n4, uint4* dst,
+                               cudaStream_t st);
 // wide: 512-request tiles (jobs of more than 256 requests), else 256
 cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, cudaStream_t st);
 constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel wins
@@ -216,9 +229,10 @@ struct tpir_db {
 namespace tpir {
 tpir_status set_error(tpir_status s);
 tpir_status cuda_status(cudaError_t e);
-// enqueue a read of db on stream (device buffers), honoring write ordering
+// enqueue a read of db on stream (device buffers), honoring write ordering;
+// d_seeds (B x 32 bytes) masks the replies (serialized PIR), null = plain
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
-                         cudaStream_t st);
+                         cudaStream_t st, const uint8_t* d_seeds = nullptr);
 // order stream `st` after the db's last write, and record a read event
 void order_after_writes(tpir_db* db, cudaStream_t st);
 void note_read(tpir_db* db, cudaStream_t st);

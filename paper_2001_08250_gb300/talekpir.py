@@ -33,7 +33,7 @@ class TpirError(RuntimeError):
 
 
 class ReadJob(ctypes.Structure):
-    _fields_ = [("db", _vp), ("B", _u32), ("d_req_bits", _vp), ("d_out", _vp)]
+    _fields_ = [("db", _vp), ("B", _u32), ("d_req_bits", _vp), ("d_out", _vp), ("d_seeds", _vp)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -81,6 +81,10 @@ _SIGS = [
     ("tpir_write_noalloc", ctypes.c_int, [_vp, _u64, _u64, _vp, _vp, _vp]),
     ("tpir_read_batch", ctypes.c_int, [_vp, _vp, _u32, _vp]),
     ("tpir_read_batch_async", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp]),
+    ("tpir_read_batch_masked", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp]),
+    ("tpir_read_batch_masked_async", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp, _vp]),
+    ("tpir_mask_generate", ctypes.c_int, [_vp, _u32, _u64, _vp, _vp]),
+    ("tpir_xor_combine", ctypes.c_int, [_vp, _u32, _u64, _vp, _vp]),
     ("tpir_db_set_kernel", ctypes.c_int, [_vp, ctypes.c_int]),
     ("tpir_read_multi_async", ctypes.c_int, [_vp, _u32, _vp]),
     ("tpir_autotune", ctypes.c_int, [_vp, _u32, _u32, _vp]),
@@ -271,6 +275,26 @@ class DB:
         _check(lib().tpir_read_batch_async(self.h, _dptr(d_req), int(B), _dptr(d_out),
                                            _stream(stream)), "tpir_read_batch_async")
 
+    def read_batch_masked(self, req_bits: np.ndarray, seeds: np.ndarray,
+                          out: np.ndarray | None = None) -> np.ndarray:
+        """Serialized-PIR read with host buffers: reply b is masked by the
+        ChaCha20 keystream of seeds[b] (uint8 [B, 32])."""
+        r = np.ascontiguousarray(req_bits, dtype=np.uint64).reshape(-1, self.words64)
+        B = r.shape[0]
+        sd = np.ascontiguousarray(seeds, dtype=np.uint8).reshape(B, 32)
+        if out is None:
+            out = np.empty((B, self.row_bytes), dtype=np.uint8)
+        assert out.flags["C_CONTIGUOUS"] and out.nbytes == B * self.row_bytes
+        _check(lib().tpir_read_batch_masked(self.h, _hptr(r), B, _hptr(sd), _hptr(out)),
+               "tpir_read_batch_masked")
+        return out
+
+    def read_batch_masked_async(self, d_req, B: int, d_seeds, d_out, stream=None) -> None:
+        """Serialized-PIR read with device buffers (d_seeds: B x 32 bytes)."""
+        _check(lib().tpir_read_batch_masked_async(self.h, _dptr(d_req), int(B), _dptr(d_seeds),
+                                                  _dptr(d_out), _stream(stream)),
+               "tpir_read_batch_masked_async")
+
     def autotune(self, B: int, reps: int = 3) -> dict:
         """Time every tile shape for B requests on this table; keep the fastest."""
         r = TuneResult()
@@ -312,25 +336,37 @@ def tune_clear() -> None:
     _check(lib().tpir_tune_clear(), "tpir_tune_clear")
 
 
-def read_multi_async(jobs, stream=None) -> None:
-    """jobs: list of (DB, B, d_req, d_out) read in one persistent launch."""
-    arr = (ReadJob * max(1, len(jobs)))()
-    for i, (db, B, d_req, d_out) in enumerate(jobs):
-        arr[i].db = db.h
-        arr[i].B = int(B)
-        arr[i].d_req_bits = _dptr(d_req)
-        arr[i].d_out = _dptr(d_out)
-    _check(lib().tpir_read_multi_async(arr, len(jobs), _stream(stream)), "tpir_read_multi_async")
+def mask_generate(d_seeds, rows: int, nbytes: int, d_out, stream=None) -> None:
+    """The one-time masks alone: rows x nbytes keystream bytes into d_out."""
+    _check(lib().tpir_mask_generate(_dptr(d_seeds), int(rows), int(nbytes), _dptr(d_out),
+                                    _stream(stream)), "tpir_mask_generate")
+
+
+def xor_combine(d_srcs, nbytes: int, d_dst, stream=None) -> None:
+    """The leader's combination: d_dst = XOR of the device buffers d_srcs."""
+    arr = (_vp * max(1, len(d_srcs)))(*[_dptr(x) for x in d_srcs])
+    _check(lib().tpir_xor_combine(arr, len(d_srcs), int(nbytes), _dptr(d_dst), _stream(stream)),
+           "tpir_xor_combine")
 
 
 def _jobs_array(jobs):
+    """jobs: tuples (DB, B, d_req, d_out) or (DB, B, d_req, d_out, d_seeds)."""
     arr = (ReadJob * max(1, len(jobs)))()
-    for i, (db, B, d_req, d_out) in enumerate(jobs):
+    for i, job in enumerate(jobs):
+        db, B, d_req, d_out = job[:4]
         arr[i].db = db.h
         arr[i].B = int(B)
         arr[i].d_req_bits = _dptr(d_req)
         arr[i].d_out = _dptr(d_out)
+        arr[i].d_seeds = _dptr(job[4]) if len(job) > 4 and job[4] is not None else None
     return arr
+
+
+def read_multi_async(jobs, stream=None) -> None:
+    """jobs: list of (DB, B, d_req, d_out[, d_seeds]) read in one persistent
+    launch per kernel kind."""
+    _check(lib().tpir_read_multi_async(_jobs_array(jobs), len(jobs), _stream(stream)),
+           "tpir_read_multi_async")
 
 
 class MultiGraph:
