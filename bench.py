@@ -41,12 +41,14 @@ COPIES = 4
 HBM_PEAK_FALLBACK = 6800.0
 SMS, LOP3_PER_CLK_PER_SM = 152, 64
 SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 bytes
-# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
-# this workload (profiles/batched_scan_kernel_paper_scale_B256.md,
-# profiles/plain_tma_kernel_paper_scale_B1.md)
-TRAFFIC_BATCHED_B256 = 136.424704e6 + 3.473152e6
+# DRAM bytes (read + write) per launch of each kernel on this workload, from
+# ncu captures summarised in profiles/ (the batched kernels: mean of three
+# launches of one capture; the plain kernel: one launch)
+TRAFFIC_BATCHED_B256 = (136.659968e6 + 3.284480e6 + 136.435200e6 + 0.130304e6 + 136.602368e6
+                        + 0.338944e6) / 3
 TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
-TRAFFIC_M4RM_B256 = 136.336896e6 + 3.187968e6
+TRAFFIC_M4RM_B256 = (136.340736e6 + 3.074048e6 + 136.585216e6 + 0.072192e6 + 136.370944e6
+                     + 0.116480e6) / 3
 
 
 def measured_peaks() -> dict:
@@ -179,9 +181,11 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--legs", default="head,head_lop3,plain,b32,e2e,serve,cpu,multi,large",
+    ap.add_argument("--legs", default="head,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large",
                     help="comma list of: head (B=256, timed headline), head_lop3 (B=256 on the "
-                         "register-tiled LOP3 kernel), plain (B=1), b32, "
+                         "register-tiled LOP3 kernel), plain (B=1), b32, masked (serialized-PIR "
+                         "masked replies at B=256 and B=1), sharded (the table in 4 row shards "
+                         "on this GPU, partial replies XOR-combined), "
                          "e2e (host buffers), serve, cpu (oracle baseline), multi (64 uneven "
                          "tables, one graph-captured launch), large (4 GiB table, B=1024); "
                          "serve_sweep (not default: tables filling a 64 GiB budget, Poisson "
@@ -243,19 +247,26 @@ def main() -> None:
     dO = torch.empty((USERS, row), dtype=torch.uint8, device="cuda")
     words = R.shape[1]
 
-    def run_step(B, events=None):
+    # one 32-byte mask seed per read, for the serialized-PIR leg
+    dS = torch.from_numpy(synth.mask_seeds(USERS, seed=1 + rank)).cuda()
+
+    def run_step(B, events=None, masked=False):
         for i, b0 in enumerate(range(0, USERS, B)):
             nb = min(B, USERS - b0)
             if events is not None:
                 events[i][0].record(stream)
-            dbs[i % COPIES].read_batch_async(dR[b0:b0 + nb], nb, dO[b0:b0 + nb], stream)
+            if masked:
+                dbs[i % COPIES].read_batch_masked_async(dR[b0:b0 + nb], nb, dS[b0:b0 + nb],
+                                                        dO[b0:b0 + nb], stream)
+            else:
+                dbs[i % COPIES].read_batch_async(dR[b0:b0 + nb], nb, dO[b0:b0 + nb], stream)
             if events is not None:
                 events[i][1].record(stream)
 
-    def timed(B, steps, warmup, with_launch_events=False, clocks=None):
+    def timed(B, steps, warmup, with_launch_events=False, clocks=None, masked=False):
         with torch.cuda.stream(stream):
             for _ in range(warmup):
-                run_step(B)
+                run_step(B, masked=masked)
         torch.cuda.synchronize()
         nb = (USERS + B - 1) // B
         ev = None
@@ -270,7 +281,7 @@ def main() -> None:
             if with_launch_events:
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                       for _ in range(nb)]
-            run_step(B, ev)
+            run_step(B, ev, masked=masked)
             if with_launch_events:
                 per_launch.append(ev)
         end.record(stream)
@@ -345,6 +356,24 @@ def main() -> None:
                          "launch_ms": launch_ms}
     plain_gbs = legs["1"]["scan_gbs"]
 
+    # ---- serialized PIR (Section 6): the same reads with one-time masks
+    masked = None
+    if "masked" in args.legs:
+        masked = {}
+        for B, steps in ((B_HEAD, max(3, args.steps // 2)), (1, max(2, args.steps // 4))):
+            mms, _, _ = timed(B, steps, 1, masked=True)
+            mms = max_over_ranks(mms)
+            base = legs[str(B)].get("ms_per_step")
+            masked[str(B)] = {"reads_per_s": USERS * world / (mms * 1e-3), "ms_per_step": mms,
+                              "overhead_vs_unmasked": (mms / base - 1.0) if base else None}
+
+    # ---- row shards (Section 9.4 scale-out) emulated on this GPU: the table in
+    # SHARDS row shards, each batch read by every shard from the same request
+    # rows, partial replies XOR-combined by the exchange's combine kernel
+    sharded = None
+    if "sharded" in args.legs and rank == 0:
+        sharded = sharded_leg(talekpir, torch, stream, T, dR, args, legs)
+
     # ---- end to end through the host-buffer entry point (pinned host memory)
     hR = torch.from_numpy(R.view(np.int64)).pin_memory().numpy().view(np.uint64)
     hO = torch.empty((USERS, row), dtype=torch.uint8).pin_memory().numpy()
@@ -410,8 +439,10 @@ def main() -> None:
             "roofline_plain": {"bound": "hbm", "achieved": plain_gbs, "peak": hbm_peak,
                                "unit": "GB/s", "frac": plain_gbs / hbm_peak,
                                "traffic": TRAFFIC_PLAIN_B1,
-                               "kernel": "plain_scan_kernel", "peak_basis": "of measured" if peaks else "of fallback"},
+                               "kernel": "plain_tma_kernel", "peak_basis": "of measured" if peaks else "of fallback"},
             "legs": legs,
+            "masked": masked,
+            "sharded": sharded,
             "autotune": tune,
             "speedup_batched_vs_plain": value / legs["1"]["reads_per_s"],
             "serve": serve,
@@ -425,6 +456,54 @@ def main() -> None:
         db.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+SHARDS = 4
+
+
+def sharded_leg(talekpir, torch, stream, T, dR, args, legs) -> dict:
+    """The paper-scale table split into SHARDS row shards on one GPU; every
+    batch of B_HEAD requests is read by all shards (full-length request rows)
+    and the partial replies XOR-combined.  Against the unsharded B_HEAD step."""
+    n, d, z = N_BUCKETS, D_SLOTS, MSG_BYTES
+    row = d * z
+    # COPIES rotated copies of every shard, as the unsharded step rotates tables
+    copies = []
+    for _ in range(COPIES):
+        shards = []
+        for begin, rows in talekpir.shard_plan(n, SHARDS):
+            db = talekpir.DB(rows, d, z, shard=(n, begin))
+            db.load(T[begin:begin + rows])
+            shards.append(db)
+        copies.append(shards)
+    nb = (USERS + B_HEAD - 1) // B_HEAD
+    parts = torch.empty((SHARDS, B_HEAD, row), dtype=torch.uint8, device="cuda")
+    out = torch.empty((USERS, row), dtype=torch.uint8, device="cuda")
+    views = [parts[i] for i in range(SHARDS)]
+
+    def step(combine=True):
+        for i in range(nb):
+            b0 = i * B_HEAD
+            m = min(B_HEAD, USERS - b0)
+            for k, db in enumerate(copies[i % COPIES]):
+                db.read_batch_async(dR[b0:b0 + m], m, parts[k, :m], stream)
+            if combine:
+                talekpir.xor_combine([v[:m] for v in views], m * row, out[b0:b0 + m],
+                                     stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    steps = max(3, args.steps // 2)
+    ms = _events_ms(torch, stream, step, steps)
+    ms_nocomb = _events_ms(torch, stream, lambda: step(False), steps)
+    base = legs.get(str(B_HEAD), {}).get("ms_per_step")
+    for shards in copies:
+        for db in shards:
+            db.close()
+    return {"shards": SHARDS, "batch": B_HEAD, "reads_per_s": USERS / (ms * 1e-3),
+            "ms_per_step": ms, "ms_partials_only": ms_nocomb,
+            "combine_ms_per_step": ms - ms_nocomb,
+            "overhead_vs_unsharded": (ms / base - 1.0) if base else None}
 
 
 def _fill_random(db, nbytes, gen, torch, stream):

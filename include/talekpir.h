@@ -67,6 +67,29 @@ const char *tpir_strerror(tpir_status s);
 tpir_db *tpir_db_create(uint64_t n, uint32_t d, uint32_t msg_bytes);
 void tpir_db_destroy(tpir_db *db);
 
+/* ---- Row shards (the scale-out Section 9.4 proposes: one server's database
+ * split over several machines, each holding a portion of it) -------------
+ * tpir_db_create_shard makes a db of `rows` buckets that stands for buckets
+ * [row_begin, row_begin + rows) of a logical table of n_total buckets
+ * (row_begin a multiple of 64, so a shard owns whole request words).  Reads
+ * on a shard take FULL-length request rows (ceil(n_total/64) words, the same
+ * buffer every shard reads) and return the shard's partial reply, the XOR of
+ * its selected buckets; the XOR of all shards' partial replies is the reply of
+ * the whole table (tpir_xor_combine is the exchange's combine step).  Masks of
+ * a masked read apply to the partial, so a sharded server masks on one shard.
+ * Shards are loaded with tpir_db_load / tpir_db_load_async (the shard's rows
+ * of the table, e.g. a snapshot of a writer's table); the cuckoo writes
+ * return TPIR_EINVAL on a shard.  NULL on error (EINVAL: shape or range). */
+tpir_db *tpir_db_create_shard(uint64_t n_total, uint64_t row_begin, uint64_t rows, uint32_t d,
+                              uint32_t msg_bytes);
+/* n_total and row_begin of a shard (n and 0 for a whole table). */
+tpir_status tpir_db_shard_info(const tpir_db *db, uint64_t *n_total, uint64_t *row_begin);
+/* Balanced split of n_total buckets into `parts` shards in whole request
+ * words (64 buckets): the range of shard `index`.  *rows is 0 for the shards
+ * left empty when parts > ceil(n_total/64).  Pure host arithmetic. */
+tpir_status tpir_shard_plan(uint64_t n_total, uint32_t parts, uint32_t index, uint64_t *row_begin,
+                            uint64_t *rows);
+
 /* Shape and state: any output pointer may be NULL.  *d_table is the device
  * address of the table; *epoch counts the writes applied so far. */
 tpir_status tpir_db_info(const tpir_db *db, uint64_t *n, uint32_t *d, uint32_t *msg_bytes,

@@ -142,6 +142,7 @@ uint32_t next_counter_slot() {
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
                          cudaStream_t st, const uint8_t* d_seeds) {
   if (B == 0) return TPIR_OK;
+  d_req += db->req_off;  // a row shard reads its own words of each request row
   order_after_writes(db, st);
   int kernel = db->forced_kernel;
   if (kernel == 0) {
@@ -278,7 +279,8 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
         (reinterpret_cast<uintptr_t>(q.d_seeds) & 15))
       return TPIR_EINVAL;
     const M4Request r{reinterpret_cast<const uint32_t*>(q.db->d_table), q.db->n, q.db->Wd,
-                      q.d_req_bits, q.db->words64, q.B, reinterpret_cast<uint32_t*>(q.d_out),
+                      q.d_req_bits + q.db->req_off, q.db->words64, q.B,
+                      reinterpret_cast<uint32_t*>(q.d_out),
                       static_cast<const uint8_t*>(q.d_seeds)};
     if (q.B >= kM4rmMinB && q.db->Wd >= 64)
       (q.B > 256 ? m4w : m4).push_back(r);
@@ -308,7 +310,7 @@ tpir_status enqueue_multi_lop3(const tpir_read_job* jobs, uint32_t njobs, cudaSt
     if ((reinterpret_cast<uintptr_t>(q.d_out) & 15) || (reinterpret_cast<uintptr_t>(q.d_req_bits) & 7) ||
         (reinterpret_cast<uintptr_t>(q.d_seeds) & 15))
       return TPIR_EINVAL;
-    ScanJob j = make_job(q.db, q.d_req_bits, q.B, q.d_out);
+    ScanJob j = make_job(q.db, q.d_req_bits + q.db->req_off, q.B, q.d_out);
     j.seeds = static_cast<const uint8_t*>(q.d_seeds);
     const double tiles = static_cast<double>((j.B + j.shape.bt() - 1) / j.shape.bt()) *
                          ((j.Wd + j.shape.wt() - 1) / j.shape.wt());
@@ -427,6 +429,40 @@ tpir_db* tpir_db_create(uint64_t n, uint32_t d, uint32_t msg_bytes) {
   return db;
 }
 
+tpir_db* tpir_db_create_shard(uint64_t n_total, uint64_t row_begin, uint64_t rows, uint32_t d,
+                              uint32_t msg_bytes) {
+  if (n_total == 0 || rows == 0 || (row_begin % 64) != 0 || row_begin >= n_total ||
+      rows > n_total - row_begin || (n_total + 63) / 64 > 0xFFFFFFFFull) {
+    set_error(TPIR_EINVAL);
+    return nullptr;
+  }
+  tpir_db* db = tpir_db_create(rows, d, msg_bytes);
+  if (!db) return nullptr;
+  db->n_total = n_total;
+  db->row_begin = row_begin;
+  db->words64 = static_cast<uint32_t>((n_total + 63) / 64);
+  db->req_off = static_cast<uint32_t>(row_begin / 64);
+  return db;
+}
+
+tpir_status tpir_db_shard_info(const tpir_db* db, uint64_t* n_total, uint64_t* row_begin) {
+  if (!db) return TPIR_EINVAL;
+  if (n_total) *n_total = db->n_total ? db->n_total : db->n;
+  if (row_begin) *row_begin = db->row_begin;
+  return TPIR_OK;
+}
+
+tpir_status tpir_shard_plan(uint64_t n_total, uint32_t parts, uint32_t index, uint64_t* row_begin,
+                            uint64_t* rows) {
+  if (n_total == 0 || parts == 0 || index >= parts || !row_begin || !rows) return TPIR_EINVAL;
+  // whole 64-bucket request words, split as evenly as possible
+  const uint64_t words = (n_total + 63) / 64;
+  const uint64_t w0 = words * index / parts, w1 = words * (index + 1) / parts;
+  *row_begin = std::min(n_total, w0 * 64);
+  *rows = std::min(n_total, w1 * 64) - *row_begin;
+  return TPIR_OK;
+}
+
 void tpir_db_destroy(tpir_db* db) {
   if (!db) return;
   if (db->stream) cudaStreamSynchronize(db->stream);
@@ -510,6 +546,7 @@ tpir_status tpir_db_dump(tpir_db* db, void* host_table, size_t bytes) {
 
 tpir_status tpir_write(tpir_db* db, uint64_t b1, uint64_t b2, const void* msg,
                        uint32_t* evictions_out) {
+  if (evictions_out) *evictions_out = 0;
   if (!db || !msg) return TPIR_EINVAL;
   tpir_status s = TPIR_OK;
   uint32_t ev = 0;
@@ -521,6 +558,7 @@ tpir_status tpir_write(tpir_db* db, uint64_t b1, uint64_t b2, const void* msg,
 tpir_status tpir_write_batch(tpir_db* db, uint32_t count, const uint64_t* b1, const uint64_t* b2,
                              const void* msgs, tpir_status* status_out, uint32_t* evictions_out) {
   if (!db || (count && (!b1 || !b2 || !msgs))) return TPIR_EINVAL;
+  if (db->n_total) return TPIR_EINVAL;  // shards hold snapshots: no cuckoo writes
   if (count == 0) return TPIR_OK;
   // the staging of the previous call must have been consumed
   cudaError_t e = cudaEventSynchronize(db->last_write);

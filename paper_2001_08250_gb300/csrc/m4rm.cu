@@ -431,21 +431,6 @@ __global__ void m4_zero_kernel(const __grid_constant__ M4Launch<NJ> L) {
                blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
-template <typename... KArgs, typename... Args>
-cudaError_t m4_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
-                      Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
 
 uint32_t m4_next_slot() {
   static std::atomic<uint32_t> next{0};
@@ -476,10 +461,10 @@ cudaError_t m4_launch_all(M4Launch<NJ>& L, cudaStream_t st) {
   bool any = false;
   for (uint32_t i = 0; i < L.njobs; ++i) any |= L.jobs[i].split != 0;
   if (any || L.dynamic)
-    e = m4_launch(m4_zero_kernel<NJ>, dim3(any ? 64 : 1, L.njobs), dim3(256), 0, st, L);
+    e = launch_pdl(m4_zero_kernel<NJ>, dim3(any ? 64 : 1, L.njobs), dim3(256), 0, st, L);
   if (e != cudaSuccess) return e;
   const uint32_t grid = std::min<uint32_t>(L.total_items, device_sm_count());
-  return m4_launch(m4rm_scan_kernel<MR, NJ>, dim3(grid), dim3(kM4Threads), M4Layout<MR>::kSmem,
+  return launch_pdl(m4rm_scan_kernel<MR, NJ>, dim3(grid), dim3(kM4Threads), M4Layout<MR>::kSmem,
                    st, L, device_status_word());
 }
 

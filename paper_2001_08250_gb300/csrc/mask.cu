@@ -11,8 +11,12 @@
 namespace tpir {
 namespace {
 
+// Both kernels are launched with PDL: they let the next kernel of the stream
+// start at once, and wait for the previous one before touching memory.
 __global__ void mask_fill_kernel(uint4* __restrict__ out, uint32_t rows, uint32_t row_u4,
                                  const uint8_t* __restrict__ seeds) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   init_replies(out, rows, row_u4, seeds, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
                (uint64_t)gridDim.x * blockDim.x);
 }
@@ -26,6 +30,8 @@ struct CombineSrcs {
 // by one thread only, so dst may be one of the sources.
 __global__ void __launch_bounds__(256) xor_combine_kernel(const __grid_constant__ CombineSrcs S,
                                                           uint64_t n4, uint4* dst) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n4;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint4 a = S.p[0][i];
@@ -48,8 +54,7 @@ cudaError_t launch_mask_fill(uint4* out, uint32_t rows, uint32_t row_u4, const u
   if (blocks == 0) return cudaSuccess;
   const uint32_t grid = static_cast<uint32_t>(
       std::min<uint64_t>((blocks + 255) / 256, static_cast<uint64_t>(device_sm_count()) * 8));
-  mask_fill_kernel<<<grid, 256, 0, st>>>(out, rows, row_u4, seeds);
-  return cudaGetLastError();
+  return launch_pdl(mask_fill_kernel, dim3(grid), dim3(256), 0, st, out, rows, row_u4, seeds);
 }
 
 cudaError_t launch_xor_combine(const uint4* const* srcs, uint32_t count, uint64_t n4, uint4* dst,
@@ -61,8 +66,7 @@ cudaError_t launch_xor_combine(const uint4* const* srcs, uint32_t count, uint64_
   S.count = count;
   const uint32_t grid = static_cast<uint32_t>(
       std::min<uint64_t>((n4 + 255) / 256, static_cast<uint64_t>(device_sm_count()) * 8));
-  xor_combine_kernel<<<grid, 256, 0, st>>>(S, n4, dst);
-  return cudaGetLastError();
+  return launch_pdl(xor_combine_kernel, dim3(grid), dim3(256), 0, st, S, n4, dst);
 }
 
 }  // namespace tpir

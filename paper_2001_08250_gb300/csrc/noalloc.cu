@@ -80,6 +80,7 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
                                           uint32_t* evictions_out, void* stream) {
   if (evictions_out) *evictions_out = 0;
   if (!db || !d_msg || (reinterpret_cast<uintptr_t>(d_msg) & 15)) return TPIR_EINVAL;
+  if (db->n_total) return TPIR_EINVAL;  // shards hold snapshots: no cuckoo writes
   if (db->z > kNoallocMaxMsgBytes) return TPIR_EINVAL;                   // slot too large
   if (db->meta->max_evictions() > kNoallocMaxEvictions) return TPIR_EINVAL;
   if (b1 >= db->n || b2 >= db->n) return TPIR_EINVAL;

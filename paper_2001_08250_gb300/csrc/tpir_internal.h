@@ -90,6 +90,25 @@ Shape choose_shape(uint32_t Wd, uint32_t B);
 bool plan_lookup(uint32_t Wd, uint32_t B, Shape* out);
 int scan_stage_bytes(const Shape& s);
 
+// Launch with programmatic dependent launch (PDL) allowed: the kernel may
+// start while the previous kernel of the stream runs; it must execute
+// griddepcontrol.wait before touching anything that kernel writes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Launch helpers (scan.cu).  All return cudaError_t of the launch.
 cudaError_t launch_batched(const ScanLaunch& L, int grid, cudaStream_t st);
 // seeds: B x 32-byte mask seeds, or null (the replies start at zero)
@@ -206,7 +225,12 @@ struct tpir_bloom_state {
 struct tpir_db {
   uint64_t n = 0;
   uint32_t d = 0, z = 0;
-  uint32_t row_bytes = 0, Wd = 0, words64 = 0;
+  uint32_t row_bytes = 0, Wd = 0, words64 = 0;  // words64: request row stride
+  // row shard of a larger logical table: buckets [row_begin, row_begin + n)
+  // of n_total (n_total = 0: a whole table); reads start req_off words into
+  // each request row
+  uint64_t n_total = 0, row_begin = 0;
+  uint32_t req_off = 0;
   int device = 0;
   uint8_t* d_table = nullptr;
   uint64_t epoch = 0;

@@ -71,6 +71,9 @@ _SIGS = [
     ("tpir_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("tpir_db_create", _vp, [_u64, _u32, _u32]),
     ("tpir_db_destroy", None, [_vp]),
+    ("tpir_db_create_shard", _vp, [_u64, _u64, _u64, _u32, _u32]),
+    ("tpir_db_shard_info", ctypes.c_int, [_vp, _vp, _vp]),
+    ("tpir_shard_plan", ctypes.c_int, [_u64, _u32, _u32, _vp, _vp]),
     ("tpir_db_info", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("tpir_db_set_policy", ctypes.c_int, [_vp, _u64, _u32, _u64]),
     ("tpir_db_load", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
@@ -177,11 +180,20 @@ def device_status() -> int:
 class DB:
     """One server's blocked cuckoo table of n buckets x d slots x msg_bytes."""
 
-    def __init__(self, n: int, d: int, msg_bytes: int):
+    def __init__(self, n: int, d: int, msg_bytes: int, shard=None):
+        """shard = (n_total, row_begin): this db holds buckets [row_begin,
+        row_begin + n) of a logical table of n_total buckets, and its reads
+        take full-length request rows (ceil(n_total/64) words)."""
         self.n, self.d, self.msg_bytes = int(n), int(d), int(msg_bytes)
         self.row_bytes = self.d * self.msg_bytes
-        self.words64 = (self.n + 63) // 64
-        h = lib().tpir_db_create(self.n, self.d, self.msg_bytes)
+        if shard is None:
+            self.n_total, self.row_begin = self.n, 0
+            h = lib().tpir_db_create(self.n, self.d, self.msg_bytes)
+        else:
+            self.n_total, self.row_begin = int(shard[0]), int(shard[1])
+            h = lib().tpir_db_create_shard(self.n_total, self.row_begin, self.n, self.d,
+                                           self.msg_bytes)
+        self.words64 = (self.n_total + 63) // 64
         if not h:
             raise TpirError(lib().tpir_last_error(), "tpir_db_create")
         self.h = h
@@ -334,6 +346,17 @@ def tune_load(path: str) -> None:
 
 def tune_clear() -> None:
     _check(lib().tpir_tune_clear(), "tpir_tune_clear")
+
+
+def shard_plan(n_total: int, parts: int) -> list[tuple[int, int]]:
+    """(row_begin, rows) of each of `parts` row shards of n_total buckets."""
+    out = []
+    for i in range(parts):
+        b, r = _u64(), _u64()
+        _check(lib().tpir_shard_plan(int(n_total), int(parts), i, ctypes.byref(b), ctypes.byref(r)),
+               "tpir_shard_plan")
+        out.append((b.value, r.value))
+    return out
 
 
 def mask_generate(d_seeds, rows: int, nbytes: int, d_out, stream=None) -> None:
