@@ -49,6 +49,8 @@ TRAFFIC_BATCHED_B256 = (136.659968e6 + 3.284480e6 + 136.435200e6 + 0.130304e6 + 
 TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
 TRAFFIC_M4RM_B256 = (136.340736e6 + 3.074048e6 + 136.585216e6 + 0.072192e6 + 136.370944e6
                      + 0.116480e6) / 3
+TRAFFIC_GF2MMA_B256 = (136.398080e6 + 2.994176e6 + 136.381440e6 + 0.123904e6 + 136.377344e6
+                       + 0.091904e6) / 3
 
 
 def measured_peaks() -> dict:
@@ -71,6 +73,20 @@ def m4rm_smem_bytes(n: int, row_words: int, B: int) -> float:
     bt = 256 if B <= 256 else 512
     groups, wtiles, btiles = (n + 7) // 8, (row_words + 63) // 64, (B + bt - 1) // bt
     return float(groups) * wtiles * (btiles * 256 * 64 * 4 + B * 64 * 4)
+
+
+def fp8_peak_tflops(peaks: dict) -> tuple[float, str]:
+    """Dense e4m3 tensor peak: the measured bf16 cuBLAS peak (burst: the kernel
+    is timed over a sub-second region) x 2, the nominal fp8 / bf16 ratio."""
+    if "bf16_tflops" in peaks:
+        return 2.0 * peaks["bf16_tflops"], "of measured (bf16 burst x 2, the nominal fp8/bf16 ratio)"
+    return 2.0 * 1900.0, "of fallback (1.9 PFLOP/s bf16 x 2)"
+
+
+def gf2_mma_flops(n: int, row_bytes: int, B: int) -> float:
+    """Tensor-core work of the GF(2) product as an integer 0/1 product:
+    one multiply-add per (request, bucket, table bit)."""
+    return 2.0 * B * n * row_bytes * 8
 
 
 def alu_peak_tops(sm_mhz: float) -> float:
@@ -181,8 +197,9 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--legs", default="head,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large",
-                    help="comma list of: head (B=256, timed headline), head_lop3 (B=256 on the "
+    ap.add_argument("--legs", default="head,head_m4rm,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large",
+                    help="comma list of: head (B=256, timed headline: the automatic choice, the "
+                         "tensor-core kernel), head_m4rm / head_lop3 (B=256 on the Four-Russians / "
                          "register-tiled LOP3 kernel), plain (B=1), b32, masked (serialized-PIR "
                          "masked replies at B=256 and B=1), sharded (the table in 4 row shards "
                          "on this GPU, partial replies XOR-combined), "
@@ -313,8 +330,26 @@ def main() -> None:
     launch_ms = statistics.mean(durs)
     ops_per_launch = B_HEAD * n * (row // 4)
     sm_mhz = (ck or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    smem_tbs = m4rm_smem_bytes(n, row // 4, B_HEAD) / (launch_ms * 1e-3) / 1e12
+    tc_peak, tc_basis = fp8_peak_tflops(peaks)
+    tc_tflops = gf2_mma_flops(n, row, B_HEAD) / (launch_ms * 1e-3) / 1e12
     smem_peak = smem_peak_tbs(sm_mhz)
+
+    # ---- the same batches on the Four-Russians kernel (shared-memory-bound)
+    m4 = None
+    if "head_m4rm" in args.legs:
+        for db in dbs:
+            db.set_kernel(4)
+        mms, mdurs, _ = timed(B_HEAD, max(3, args.steps // 2), 1, with_launch_events=True)
+        for db in dbs:
+            db.set_kernel(0)
+        mms = max_over_ranks(mms)
+        m_launch = statistics.mean(mdurs)
+        m_tbs = m4rm_smem_bytes(n, row // 4, B_HEAD) / (m_launch * 1e-3) / 1e12
+        m4 = {"reads_per_s": USERS * world / (mms * 1e-3), "ms_per_step": mms, "launch_ms": m_launch,
+              "roofline": {"bound": "smem", "achieved": m_tbs, "peak": smem_peak, "unit": "TB/s",
+                           "frac": m_tbs / smem_peak, "traffic": TRAFFIC_M4RM_B256,
+                           "kernel": "m4rm_scan_kernel",
+                           "peak_basis": f"{SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk shared memory x {sm_mhz:.0f} MHz"}}
 
     # ---- the same batches on the register-tiled LOP3 kernel (ALU-bound)
     lop3 = None
@@ -429,12 +464,13 @@ def main() -> None:
             "data": "synthetic", "config": workload_config(args),
             "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": ck,
-            "roofline": {"bound": "smem", "achieved": smem_tbs, "peak": smem_peak,
-                         "unit": "TB/s", "frac": smem_tbs / smem_peak,
-                         "traffic": TRAFFIC_M4RM_B256,
-                         "kernel": "m4rm_scan_kernel (+ m4_zero_kernel)",
-                         "peak_basis": f"{SMS} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk shared memory x {sm_mhz:.0f} MHz (median SM clock sampled)",
+            "roofline": {"bound": "tensor", "achieved": tc_tflops, "peak": tc_peak,
+                         "unit": "TFLOP/s", "frac": tc_tflops / tc_peak,
+                         "traffic": TRAFFIC_GF2MMA_B256,
+                         "kernel": "gf2_mma_kernel (tcgen05 kind::f8f6f4, e4m3 0/1 operands)",
+                         "peak_basis": tc_basis,
                          "lop3_equivalent_tops": ops_per_launch / (launch_ms * 1e-3) / 1e12},
+            "head_m4rm": m4,
             "head_lop3": lop3,
             "roofline_plain": {"bound": "hbm", "achieved": plain_gbs, "peak": hbm_peak,
                                "unit": "GB/s", "frac": plain_gbs / hbm_peak,
@@ -593,6 +629,9 @@ def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:
     O = torch.empty((B, d * z), dtype=torch.uint8, device="cuda")
     db.read_batch_async(R, B, O, stream)
     bms = _events_ms(torch, stream, lambda: db.read_batch_async(R, B, O, stream), 3)
+    db.set_kernel(4)
+    db.read_batch_async(R, B, O, stream)
+    mms = _events_ms(torch, stream, lambda: db.read_batch_async(R, B, O, stream), 2)
     db.set_kernel(2)
     db.read_batch_async(R, B, O, stream)
     lms = _events_ms(torch, stream, lambda: db.read_batch_async(R, B, O, stream), 2)
@@ -605,10 +644,12 @@ def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:
     return {"n": n, "d": d, "msg_bytes": z, "B": B, "table_bytes": tb,
             "batched_ms": bms, "batched_reads_per_s": B / (bms * 1e-3),
             "batched_lop3_equivalent_tops": ops / (bms * 1e-3) / 1e12,
-            "batched_kernel": "m4rm_scan_kernel (automatic choice at B = 1024)",
+            "batched_kernel": "gf2_mma_kernel (automatic choice at B = 1024)",
+            "batched_tensor_tflops": gf2_mma_flops(n, d * z, B) / (bms * 1e-3) / 1e12,
+            "m4rm_kernel_ms": mms, "m4rm_kernel_reads_per_s": B / (mms * 1e-3),
             "lop3_kernel_ms": lms, "lop3_kernel_reads_per_s": B / (lms * 1e-3),
             "lop3_kernel_frac_at_2070MHz": ops / (lms * 1e-3) / 1e12 / alu_peak_tops(2070.0),
-            "m4rm_smem_frac_at_2070MHz": m4rm_smem_bytes(n, d * z // 4, B) / (bms * 1e-3) / 1e12 / smem_peak_tbs(2070.0),
+            "m4rm_smem_frac_at_2070MHz": m4rm_smem_bytes(n, d * z // 4, B) / (mms * 1e-3) / 1e12 / smem_peak_tbs(2070.0),
             "plain_ms": pms, "plain_reads_per_s": 1.0 / (pms * 1e-3),
             "plain_scan_gbs": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9,
             "plain_frac_hbm": (tb + n / 8 + d * z) / (pms * 1e-3) / 1e9 / hbm_peak}

@@ -192,13 +192,15 @@ tpir_status tpir_xor_combine(const void *const *d_srcs, uint32_t count, uint64_t
                              void *d_dst, void *stream);
 
 /* Force a kernel choice for tests and benchmarks: 0 = automatic (plain for
- * B <= 4, Four-Russians for B >= 176 on rows of >= 256 bytes, register-tiled
+ * B <= 4, tensor-core for B >= 96 on rows of >= 256 bytes, register-tiled
  * batched otherwise), 1 = plain streaming kernel (B <= 4 per launch,
  * larger B is split into launches; TMA-staged where the row width allows),
  * 2 = batched register-tiled kernel, 3 = plain kernel with register
  * streaming only (the path used for row widths the TMA-staged one skips),
  * 4 = batched Four-Russians kernel (groups of 8 buckets, 256 combinations in
- * shared memory, one lookup per request and group). */
+ * shared memory, one lookup per request and group), 5 = batched tensor-core
+ * kernel (the GF(2) product as an exact integer product of 0/1 matrices on
+ * tcgen05, e4m3 operands, fp32 accumulators, reduced mod 2). */
 tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
 
 /* Autotuner of the batched kernel's tile shape: times every admissible shape

@@ -146,13 +146,14 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
   order_after_writes(db, st);
   int kernel = db->forced_kernel;
   if (kernel == 0) {
-    // plain stream for a few requests; the Four-Russians kernel once the batch
-    // amortises its per-group combination tables (measured crossover on
-    // GB300: B ~ 170 for 4 KiB rows); the register-tiled kernel in between
+    // plain stream for a few requests; the tensor-core kernel once its
+    // 128-request M-tiles are well filled (measured crossover with the
+    // register-tiled kernel on GB300: B ~ 96 for 4 KiB rows); the
+    // register-tiled kernel in between
     if (B <= kPlainMaxB)
       kernel = 1;
-    else if (B >= kM4rmMinB && db->Wd >= 64)
-      kernel = 4;
+    else if (B >= kTensorMinB && db->Wd >= 64)
+      kernel = 5;
     else
       kernel = 2;
   }
@@ -168,6 +169,9 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
                        d_seeds ? d_seeds + static_cast<uint64_t>(b0) * 32 : nullptr, st,
                        kernel == 3 ? -1 : 0);
     }
+  } else if (kernel == 5) {
+    e = launch_gf2_mma(reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, d_req,
+                       db->words64, B, reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
   } else if (kernel == 4) {
     e = launch_m4rm(reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, d_req,
                     db->words64, B, reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
@@ -504,7 +508,7 @@ tpir_status tpir_db_set_policy(tpir_db* db, uint64_t capacity, uint32_t max_evic
 }
 
 tpir_status tpir_db_set_kernel(tpir_db* db, int kernel) {
-  if (!db || kernel < 0 || kernel > 4) return TPIR_EINVAL;
+  if (!db || kernel < 0 || kernel > 5) return TPIR_EINVAL;
   db->forced_kernel = kernel;
   return TPIR_OK;
 }

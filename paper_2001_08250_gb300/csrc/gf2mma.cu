@@ -1,0 +1,600 @@
+// Tensor-core form of the batched PIR read (Section 2 step 5, batched as in
+// Section 9.2): Out = R (x) T over GF(2).  Each output bit is the parity of
+// an integer: the number of buckets k with request bit R[b][k] = 1 and table
+// bit T[k][c] = 1.  The kernel computes these integers exactly as a product
+// of 0/1 matrices on the 5th-generation tensor cores (tcgen05.mma,
+// kind::f8f6f4, e4m3 operands, fp32 accumulators in tensor memory) and keeps
+// the low bit of each: exactly the XOR of the selected buckets, with every
+// bucket read for every request as in the scalar kernels.
+//
+// Shapes.  An item is (256-bit column strip of the table = 8 words of every
+// row, block of up to 256 requests = two M-tiles of 128, k-chunk of buckets).
+// The MMA is M = 128 requests x N = 256 columns x K = 32 buckets.
+//
+// Data flow per CTA (persistent, one per SM, 416 threads):
+//   warp 12     streams the strip (8 words of 128 rows per stage) with 2-D TMA
+//               loads into a 6-deep ring of raw stages, ahead of use;
+//   warps 0-3   table producers: each takes 32 rows of a raw stage, one row
+//               per lane, and writes the row's 256 bits as e4m3 bytes (a set
+//               bit = 2^-6) into the B operand, which is MN-major (columns
+//               contiguous), so a table row needs no transposition;
+//   warps 4-7   request producers: expand each request's 128 bits of the
+//               stage into the other operand (the next stage's words are
+//               loaded while the current one is expanded);
+//   warp 8 lane 0 issues the MMAs of each stage into the item's accumulators
+//               and commits them to the stage's "empty" barrier;
+//   warps 8-11  epilogue: read the accumulators (tcgen05.ld), take each sum's
+//               parity, and store (single k-chunk) or XOR-reduce (split, or a
+//               masked read) the reply words.
+// Stages: 3 x 64 KiB ring (A: 2 x 128 requests x 128 buckets, K-major; B:
+// 256 columns x 128 buckets, MN-major).  Accumulators: 2 x 256 TMEM columns (two M-tiles of one
+// item, or two items of one M-tile each, double-buffered).  Every wait is
+// bounded; a wait that gives up sets the status word, the CTA drains its MMAs
+// and frees its tensor memory before it returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "mbar.cuh"
+#include "tpir_internal.h"
+
+namespace tpir {
+namespace {
+
+constexpr int kGStages = 3;
+constexpr int kGKStage = 128;                    // buckets per stage
+constexpr int kGKStep = 32;                      // buckets per MMA (32 e4m3 bytes of K)
+constexpr int kGWords = 8;                       // table words per strip (256 columns)
+constexpr int kGTile = 128 * kGKStage;           // 128 operand rows of one stage: 16 KiB
+constexpr int kGStageBytes = 4 * kGTile;         // A: 2 tiles, B: 2 tiles
+constexpr int kGSbo = (kGKStage / 16) * 128;     // A: bytes between 8-row core-matrix groups
+constexpr int kGLbo = 128;                       // A: bytes between 16-byte K chunks
+constexpr int kGSboB = (kGKStage / 8) * 128;     // B: bytes between 16-column groups
+constexpr int kGLboB = 128;                      // B: bytes between 8-bucket K groups
+constexpr int kGThreads = 416;
+constexpr int kGRaw = 6;                         // raw table stages in flight
+constexpr int kGRawBytes = 128 * kGWords * 4;    // 128 rows x 8 words: 4 KiB
+constexpr int kGSmem = 1024 + kGStages * kGStageBytes + kGRaw * kGRawBytes;
+constexpr uint32_t kGTmemCols = 512;
+constexpr uint64_t kGWaitNs = 4000000000ull;
+constexpr uint32_t kGOne = 0x08u;                // e4m3 2^-6: the value of a set bit
+constexpr uint64_t kGMaxCount = 32768;           // largest count one accumulator holds
+
+// Instruction descriptor: D fp32, A and B e4m3, A K-major, B MN-major (bit
+// 16), N = 256, M = 128.
+constexpr uint32_t kGIdesc = (1u << 4) | (1u << 16) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct GLaunch {
+  const uint32_t* T;
+  const uint64_t* R;
+  uint32_t* out;
+  uint64_t n;
+  uint32_t Wd, words64, B;
+  uint32_t n_strips, n_mb, kc_rows, total_items;
+  uint32_t split, nbuf;
+};
+
+struct GItem {
+  uint32_t strip, b0, mt;
+  uint64_t k0, k1;
+};
+
+__device__ __forceinline__ GItem g_decode(const GLaunch& L, uint32_t item) {
+  GItem it;
+  it.strip = item % L.n_strips;
+  const uint32_t rest = item / L.n_strips;
+  const uint32_t mb = rest % L.n_mb;
+  it.k0 = static_cast<uint64_t>(rest / L.n_mb) * L.kc_rows;
+  it.k1 = min(L.n, it.k0 + L.kc_rows);
+  it.b0 = mb * 256u;
+  const uint32_t left = L.B - it.b0;
+  it.mt = left > 128u ? 2u : 1u;
+  return it;
+}
+
+// Position in this CTA's sequence of stages (item r, stage start ks); every
+// role walks the same sequence.
+struct GCursor {
+  uint32_t r;
+  uint64_t ks;
+  GItem it;
+  bool valid;
+};
+__device__ __forceinline__ void g_cur_item(GCursor& c, const GLaunch& L) {
+  const uint32_t item = blockIdx.x + c.r * gridDim.x;
+  c.valid = item < L.total_items;
+  if (c.valid) {
+    c.it = g_decode(L, item);
+    c.ks = c.it.k0;
+  }
+}
+__device__ __forceinline__ GCursor g_cur_start(const GLaunch& L) {
+  GCursor c;
+  c.r = 0;
+  g_cur_item(c, L);
+  return c;
+}
+__device__ __forceinline__ void g_cur_next(GCursor& c, const GLaunch& L) {
+  c.ks += kGKStage;
+  if (c.ks >= c.it.k1) {
+    ++c.r;
+    g_cur_item(c, L);
+  }
+}
+
+// Shared-memory matrix descriptors without swizzle.  K-major (A): 8-row x
+// 16-byte core matrices, kGLbo apart along K, kGSbo apart along M.  MN-major
+// (B): 16-column x 8-bucket core matrices (each bucket's 16 columns
+// contiguous), kGLboB apart along K, kGSboB apart along N.
+__device__ __forceinline__ uint64_t g_desc_sw(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(lbo >> 4) << 16) |
+         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ uint64_t g_desc(uint32_t addr) { return g_desc_sw(addr, kGLbo, kGSbo); }
+__device__ __forceinline__ uint64_t g_desc_b(uint32_t addr) { return g_desc_sw(addr, kGLboB, kGSboB); }
+
+// byte offset of (row, k) in the K-major A operand of a stage
+__device__ __forceinline__ uint32_t g_off(uint32_t row, uint32_t kbyte) {
+  return (row >> 3) * kGSbo + (kbyte >> 4) * kGLbo + (row & 7u) * 16u;
+}
+// byte offset of (16-column group g, bucket k) in the MN-major B operand
+__device__ __forceinline__ uint32_t g_off_b(uint32_t g, uint32_t k) {
+  return g * kGSboB + (k >> 3) * kGLboB + (k & 7u) * 16u;
+}
+
+// Bits 4a..4a+3 of x as four e4m3 bytes (kGOne or 0): spreads the nibble to
+// bit 3 of each byte with one multiply (the four shifted copies never overlap).
+__device__ __forceinline__ uint32_t g_nib(uint32_t x, int a) {
+  static_assert(kGOne == 0x08u, "the multiply below lands each bit on bit 3 of its byte");
+  return (((x >> (4 * a)) & 0xFu) * 0x01020408u) & (kGOne * 0x01010101u);
+}
+// 16 bits (bits 16h..16h+15 of x) as one 16-byte chunk of operand bytes
+__device__ __forceinline__ uint4 g_chunk(uint32_t x, int h) {
+  return make_uint4(g_nib(x, 4 * h), g_nib(x, 4 * h + 1), g_nib(x, 4 * h + 2), g_nib(x, 4 * h + 3));
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+
+// 2-D TMA load of a box (8 words x 128 rows at word x, row y) into shared
+// memory, completing `bytes` on the mbarrier
+__device__ __forceinline__ void g_tma_load(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                           uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb::saddr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mb::saddr(bar))
+      : "memory");
+}
+
+// the request words of one stage: this thread's request in each M-tile,
+// buckets ks .. ks + 127 (zeros past the request rows and the batch)
+__device__ __forceinline__ void g_req_load(const GLaunch& L, const GCursor& c, uint32_t q,
+                                           uint64_t (&x)[4]) {
+  const uint64_t wi = c.ks >> 6;
+#pragma unroll
+  for (uint32_t t = 0; t < 2; ++t) {
+    const uint32_t b = c.it.b0 + 128u * t + q;
+    x[2 * t] = x[2 * t + 1] = 0ull;
+    if (c.valid && t < c.it.mt && b < L.B) {
+      const uint64_t* rq = L.R + static_cast<uint64_t>(b) * L.words64;
+      x[2 * t] = __ldg(rq + wi);
+      if (wi + 1 < L.words64) x[2 * t + 1] = __ldg(rq + wi + 1);
+    }
+  }
+}
+
+__device__ __forceinline__ void g_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                      uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kGIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void g_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   mb::saddr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void g_red_xor64(uint32_t* p, uint32_t lo, uint32_t hi) {
+  const uint64_t v = (static_cast<uint64_t>(hi) << 32) | lo;
+  asm volatile("red.relaxed.gpu.global.xor.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Parity word of 32 accumulator columns: each value is an exact count times
+// 2^-12; scaling by 2^12 and adding 2^23 puts the count in the mantissa, whose
+// lowest bit is the count's parity.
+__device__ __forceinline__ uint32_t g_parity_word(const uint32_t (&r)[32]) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    w |= (__float_as_uint(fmaf(__uint_as_float(r[j]), 4096.f, 8388608.f)) & 1u) << j;
+  return w;
+}
+
+__device__ __forceinline__ void g_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kGThreads, 1)
+    gf2_mma_kernel(const __grid_constant__ GLaunch L, const __grid_constant__ CUtensorMap tmap,
+                   int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], accf[2], acce[2], drain;
+  __shared__ __align__(8) uint64_t raw_full[kGRaw], raw_empty[kGRaw];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  uint8_t* stages = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t stage0 = mb::saddr(stages);
+  const uint32_t raw0 = stage0 + kGStages * kGStageBytes;
+  volatile int* abort_flag = &s_abort;
+
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGStages; ++s) {
+      mb::init(&full[s], 256);
+      mb::init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mb::init(&accf[b], 1);
+      mb::init(&acce[b], 128);
+    }
+    mb::init(&drain, 1);
+    for (int s = 0; s < kGRaw; ++s) {
+      mb::init(&raw_full[s], 1);
+      mb::init(&raw_empty[s], 4);
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     mb::saddr(&s_tmem)),
+                 "r"(kGTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 12) {
+    // ------------------------- table strip loads (TMA) -------------------------
+    if (lane == 0) {
+      uint32_t p = 0;
+      for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++p) {
+        const uint32_t rs = p % kGRaw, ph = (p / kGRaw) & 1u;
+        if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
+        g_tma_load(raw0 + rs * kGRawBytes, &tmap, static_cast<int>(c.it.strip * kGWords),
+                   static_cast<int>(c.ks), &raw_full[rs], kGRawBytes);
+      }
+      // Loads still landing (an aborted run) complete before the CTA exits: a
+      // slot has at most one load in flight, its latest, so its phase parity
+      // is unambiguous.
+      for (uint32_t rs = 0; rs < static_cast<uint32_t>(kGRaw) && rs < p; ++rs) {
+        const uint32_t last = rs + kGRaw * ((p - 1 - rs) / kGRaw);
+        const uint64_t t0 = mb::gtimer();
+        while (!mb::try_wait(&raw_full[rs], (last / kGRaw) & 1u)) {
+          if (mb::gtimer() - t0 > kGWaitNs) {
+            atomicExch(status, static_cast<int>(TPIR_ETIMEDOUT));
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp < 4) {
+    // ------------------------ table expanders ------------------------
+    uint32_t iter = 0;
+    for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter) {
+      const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
+      const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
+      if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) break;
+      // row ks + 32 warp + lane of the strip (zeros past the table: TMA fill)
+      const uint32_t ra = raw0 + rs * kGRawBytes + (32u * warp + lane) * (kGWords * 4);
+      const uint4 a = ld_shared_v4(ra), b = ld_shared_v4(ra + 16);
+      if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
+      uint32_t used = 0;
+      if (c.ks + 32u * warp < c.it.k1) {
+        const uint32_t w[kGWords] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        const uint32_t o = stage0 + s * kGStageBytes + 2 * kGTile + g_off_b(0, 32u * warp + lane);
+#pragma unroll
+        for (int i = 0; i < kGWords; ++i) {
+          st_shared_v4(o + (2 * i) * kGSboB, g_chunk(w[i], 0));      // columns 32 i .. 32 i + 15
+          st_shared_v4(o + (2 * i + 1) * kGSboB, g_chunk(w[i], 1));  // columns 32 i + 16 .. 32 i + 31
+        }
+      } else {
+        used = a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+      }
+      // The raw slot goes back to the TMA warp only once this warp's loads
+      // from it have landed (their values are consumed above) and are ordered
+      // before the async proxy's next write to the slot: a shared load still
+      // in flight at the release could read the next stage's rows.
+      asm volatile("fence.proxy.async.shared::cta;" ::"r"(used) : "memory");
+      __syncwarp();
+      if (lane == 0) mb::arrive(&raw_empty[rs]);
+      mb::arrive(&full[s]);
+    }
+  } else if (warp < 8) {
+    // ------------------------ request expanders ------------------------
+    const uint32_t q = threadIdx.x - 128u;
+    uint32_t iter = 0;
+    GCursor c = g_cur_start(L);
+    uint64_t nx[4];
+    g_req_load(L, c, q, nx);
+    while (c.valid) {
+      const uint64_t x[4] = {nx[0], nx[1], nx[2], nx[3]};
+      GCursor nc = c;
+      g_cur_next(nc, L);
+      g_req_load(L, nc, q, nx);  // the next stage's words, in flight meanwhile
+      const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
+      if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
+      const uint32_t st = stage0 + s * kGStageBytes;
+#pragma unroll
+      for (uint32_t t = 0; t < 2; ++t) {
+        const uint32_t b = c.it.b0 + 128u * t + q;
+        if (t < c.it.mt && b < L.B) {
+          const uint32_t xw[4] = {static_cast<uint32_t>(x[2 * t]), static_cast<uint32_t>(x[2 * t] >> 32),
+                                  static_cast<uint32_t>(x[2 * t + 1]),
+                                  static_cast<uint32_t>(x[2 * t + 1] >> 32)};
+          const uint32_t abase = st + t * kGTile;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) st_shared_v4(abase + g_off(q, 16u * k), g_chunk(xw[k >> 1], k & 1));
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mb::arrive(&full[s]);
+      c = nc;
+      ++iter;
+    }
+  } else {
+    // ------------------------- MMA issue + epilogue -------------------------
+    const uint32_t ew = warp - 8;  // tensor-memory lanes 32 ew .. 32 ew + 31
+    const uint32_t lag = L.nbuf - 1;
+    uint32_t iter = 0;
+    bool pdl_waited = false;
+    for (uint32_t r = 0;; ++r) {
+      const uint32_t item = blockIdx.x + r * gridDim.x;
+      const bool issue = item < L.total_items;
+      if (warp == 8) {
+        if (issue && lane == 0 && !*abort_flag) {
+          const GItem it = g_decode(L, item);
+          const uint32_t buf = L.nbuf == 2 ? (r & 1u) : 0u;
+          const uint32_t acc = tmem + buf * 256u;
+          bool ok = true;
+          if (r >= L.nbuf)
+            ok = mb::wait_sleep(&acce[buf], ((r / L.nbuf) - 1u) & 1u, abort_flag, status, kGWaitNs, 64);
+          for (uint64_t ks = it.k0; ok && ks < it.k1; ks += kGKStage, ++iter) {
+            const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
+            if (!mb::wait(&full[s], ph, abort_flag, status, kGWaitNs)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = stage0 + s * kGStageBytes;
+            const uint64_t left = it.k1 - ks;
+            const uint32_t nk = left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
+            for (uint32_t j = 0; j < nk; ++j)
+              for (uint32_t t = 0; t < it.mt; ++t)
+                g_mma(acc + 256u * t, g_desc(st + t * kGTile + 2u * kGLbo * j),
+                      g_desc_b(st + 2 * kGTile + 4u * kGLboB * j), (ks > it.k0 || j > 0) ? 1u : 0u);
+            g_commit(&empty[s]);
+          }
+          if (ok) g_commit(&accf[buf]);
+        }
+        __syncwarp();
+      }
+      if (r < lag) {
+        if (!issue) break;
+        continue;
+      }
+      // epilogue of item e
+      const uint32_t e = r - lag;
+      const uint32_t eitem = blockIdx.x + e * gridDim.x;
+      if (eitem >= L.total_items || *abort_flag) break;
+      const GItem it = g_decode(L, eitem);
+      const uint32_t buf = L.nbuf == 2 ? (e & 1u) : 0u;
+      if (!mb::wait_sleep(&accf[buf], (e / L.nbuf) & 1u, abort_flag, status, kGWaitNs, 256)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!pdl_waited) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");  // replies initialised / released
+        pdl_waited = true;
+      }
+      const uint32_t w0 = it.strip * kGWords;
+      for (uint32_t t = 0; t < it.mt; ++t) {
+        const uint32_t b = it.b0 + 128u * t + 32u * ew + lane;
+        uint32_t pw[kGWords];
+#pragma unroll
+        for (int c = 0; c < kGWords; ++c) {
+          pw[c] = 0u;
+          if (w0 + c < L.Wd) {  // uniform across the warp
+            uint32_t v[32];
+            g_ld32(tmem + buf * 256u + 256u * t + 32u * c + ((32u * ew) << 16), v);
+            pw[c] = g_parity_word(v);
+          }
+        }
+        if (b < L.B) {
+          uint32_t* o = L.out + static_cast<uint64_t>(b) * L.Wd + w0;
+          if (L.split) {
+#pragma unroll
+            for (int c = 0; c < kGWords; c += 2) {
+              if (w0 + c + 1 < L.Wd)
+                g_red_xor64(o + c, pw[c], pw[c + 1]);
+              else if (w0 + c < L.Wd)
+                atomicXor(o + c, pw[c]);
+            }
+          } else if (w0 + kGWords <= L.Wd) {
+            reinterpret_cast<uint4*>(o)[0] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+            reinterpret_cast<uint4*>(o)[1] = make_uint4(pw[4], pw[5], pw[6], pw[7]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < kGWords; ++c)
+              if (w0 + c < L.Wd) o[c] = pw[c];
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mb::arrive(&acce[buf]);
+    }
+  }
+
+  // Drain: every MMA this CTA issued completes before its tensor memory is
+  // freed (a no-op wait on the normal path; bounded on an aborted one).
+  if (warp == 8 && lane == 0) {
+    g_commit(&drain);
+    const uint64_t t0 = mb::gtimer();
+    while (!mb::try_wait(&drain, 0)) {
+      if (mb::gtimer() - t0 > kGWaitNs) {
+        atomicExch(status, static_cast<int>(TPIR_ETIMEDOUT));
+        break;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 8)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kGTmemCols)
+                 : "memory");
+}
+
+// Tensor map of a table as a 2-D array of 32-bit words (Wd x n), box 8 words
+// x 128 rows; encoded once per (table, shape) through the driver entry point.
+cudaError_t g_table_map(const uint32_t* T, uint64_t n, uint32_t Wd, CUtensorMap* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, uint64_t, uint32_t>, CUtensorMap> cache;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple(static_cast<const void*>(T), n, Wd);
+  const auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {Wd, n};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Wd) * 4};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kGWords), 128};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(T), dims,
+                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  if (cache.size() > 4096) cache.clear();
+  cache[key] = m;
+  *out = m;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
+                           uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+                           cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  int* status = device_status_word();
+  if (!status) return cudaErrorInvalidSymbol;
+  static bool ready = false;
+  if (!ready) {
+    cudaError_t e = cudaFuncSetAttribute(gf2_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kGSmem);
+    if (e != cudaSuccess) return e;
+    ready = true;
+  }
+  GLaunch L{};
+  L.T = T;
+  L.R = R;
+  L.out = out;
+  L.n = n;
+  L.Wd = Wd;
+  L.words64 = words64;
+  L.B = B;
+  L.n_strips = (Wd + kGWords - 1) / kGWords;
+  L.n_mb = (B + 255) / 256;
+  L.nbuf = B <= 128 ? 2u : 1u;
+  const int grid = device_sm_count();
+  // k-chunks (multiples of a stage) minimising rounds x item time on the grid;
+  // item time ~ MMAs (147 cycles each at N = 256, K = 32) + epilogue, which the
+  // second accumulator hides when an item holds one M-tile
+  const double mts = B <= 128 ? 1.0 : 2.0;
+  const double epi = L.nbuf == 2 ? 600.0 : 2500.0;
+  // (a k-chunk's counts stay below kGMaxCount, the range in which the fp32
+  // accumulators were checked exact, whatever the tensor cores' internal
+  // accumulation width)
+  const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
+  const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
+  double best = 1e300;
+  uint64_t best_rows = kGKStage;
+  for (uint64_t c = std::max<uint64_t>(1, min_kc); c <= std::max<uint64_t>(min_kc, std::min<uint64_t>(max_kc, 512)); ++c) {
+    uint64_t rows = (n + c - 1) / c;
+    rows = (rows + kGKStage - 1) / kGKStage * kGKStage;
+    if (rows > kGMaxCount) continue;
+    const uint64_t kcs = (n + rows - 1) / rows;
+    const uint64_t items = static_cast<uint64_t>(L.n_strips) * L.n_mb * kcs;
+    const uint64_t rounds = (items + grid - 1) / grid;
+    const double cost = static_cast<double>(rounds) *
+                        (static_cast<double>(rows) / kGKStep * mts * 147.0 + epi);
+    if (cost < best) {
+      best = cost;
+      best_rows = rows;
+    }
+  }
+  L.kc_rows = static_cast<uint32_t>(std::min<uint64_t>(best_rows, 0x7FFFFF80ull));
+  const uint64_t kcs = (n + L.kc_rows - 1) / L.kc_rows;
+  const uint64_t items = static_cast<uint64_t>(L.n_strips) * L.n_mb * kcs;
+  if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  L.total_items = static_cast<uint32_t>(items);
+  L.split = (kcs > 1 || seeds) ? 1u : 0u;
+  CUtensorMap tmap;
+  cudaError_t e = g_table_map(T, n, Wd, &tmap);
+  if (e != cudaSuccess) return e;
+  if (L.split) e = launch_init_replies(reinterpret_cast<uint4*>(out), B, Wd / 4, seeds, st);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(gf2_mma_kernel, dim3(static_cast<uint32_t>(std::min<uint64_t>(items, grid))),
+                    dim3(kGThreads), kGSmem, st, L, tmap, status);
+}
+
+}  // namespace tpir

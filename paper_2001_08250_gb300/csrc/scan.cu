@@ -911,17 +911,24 @@ static bool plain_tma_ok(uint32_t U, int nb) {
   return (U % 256) == 0 && (c == 1 || c == 2 || c == 4 || c == 8) && c <= cmax;
 }
 
+cudaError_t launch_init_replies(uint4* out, uint32_t B, uint32_t row_u4, const uint8_t* seeds,
+                                cudaStream_t st) {
+  // one thread per 16-byte word (zeros) or per 64-byte keystream block (masks)
+  const uint64_t work = seeds ? static_cast<uint64_t>(B) * ((row_u4 + 3) / 4)
+                              : static_cast<uint64_t>(B) * row_u4;
+  if (work == 0) return cudaSuccess;
+  return launch_pdl(init_replies_kernel,
+                    dim3(static_cast<uint32_t>(std::min<uint64_t>((work + 255) / 256, 1024))),
+                    dim3(256), 0, st, out, B, row_u4, seeds);
+}
+
 cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
                          uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                          cudaStream_t st, int ctas) {
   if (B == 0) return cudaSuccess;
   const uint32_t U = Wd / 4;
   uint4* o4 = reinterpret_cast<uint4*>(out);
-  // one thread per 16-byte word (zeros) or per 64-byte keystream block (masks)
-  const uint64_t work = seeds ? static_cast<uint64_t>(B) * ((U + 3) / 4) : static_cast<uint64_t>(B) * U;
-  cudaError_t e = launch_pdl(init_replies_kernel,
-                             dim3(static_cast<uint32_t>(std::min<uint64_t>((work + 255) / 256, 1024))),
-                             dim3(256), 0, st, o4, B, U, seeds);
+  cudaError_t e = launch_init_replies(o4, B, U, seeds, st);
   if (e != cudaSuccess) return e;
   const int nb = B == 1 ? 1 : (B == 2 ? 2 : 4);
   const uint4* T4 = reinterpret_cast<const uint4*>(T);

@@ -116,6 +116,15 @@ cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint6
                          uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                          cudaStream_t st, int ctas);
 cudaError_t launch_zero_outputs(const ScanLaunch& L, cudaStream_t st);
+// Initialises B replies of row_u4 16-byte words before a scan XOR-reduces into
+// them: zeros, or the masks of `seeds` (PDL-chained).
+cudaError_t launch_init_replies(uint4* out, uint32_t B, uint32_t row_u4, const uint8_t* seeds,
+                                cudaStream_t st);
+// Tensor-core batched read (gf2mma.cu): the GF(2) product as an exact integer
+// product of 0/1 matrices on tcgen05, reduced mod 2.
+cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
+                           uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+                           cudaStream_t st);
 int device_sm_count();
 int plain_ctas_per_sm();
 int batched_ctas_per_sm();
@@ -162,7 +171,8 @@ cudaError_t launch_xor_combine(const uint4* const* srcs, uint32_t count, uint64_
                                cudaStream_t st);
 // wide: 512-request tiles (jobs of more than 256 requests), else 256
 cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, cudaStream_t st);
-constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel wins
+constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel beats LOP3
+constexpr uint32_t kTensorMinB = 96;  // batch from which the tensor-core kernel beats LOP3
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
 
 // Host cuckoo metadata (cuckoo.cpp): same placement rules as the paper's

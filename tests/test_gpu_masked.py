@@ -16,7 +16,7 @@ from paper_2001_08250_gb300 import synth, talekpir
 
 pytestmark = pytest.mark.gpu
 
-PLAIN, BATCHED, PLAIN_REG, M4RM = 1, 2, 3, 4
+PLAIN, BATCHED, PLAIN_REG, M4RM, TENSOR = 1, 2, 3, 4, 5
 
 EDGE = [
     (1, 1, 16, 1), (63, 1, 16, 3), (64, 2, 48, 9), (65, 4, 16, 31), (200, 8, 32, 33),
@@ -37,7 +37,7 @@ def _seeds_dev(S):
 
 
 @pytest.mark.parametrize("n,d,z,B", EDGE)
-@pytest.mark.parametrize("kernel", [PLAIN, BATCHED, PLAIN_REG, M4RM])
+@pytest.mark.parametrize("kernel", [PLAIN, BATCHED, PLAIN_REG, M4RM, TENSOR])
 def test_masked_edge_shapes_bit_exact(n, d, z, B, kernel):
     require_cuda()
     T = synth.table_bytes(n, d, z, seed=61, table=n * 5 + d)
@@ -72,7 +72,7 @@ def test_masked_paper_scale_sampled():
         Out = to_host(dO)
         exp = oracle.read_batch_masked(T, n, d, z, R[rows], S[rows])
         assert np.array_equal(Out[rows], exp)
-        for k in (BATCHED, M4RM):
+        for k in (BATCHED, M4RM, TENSOR):
             db.set_kernel(k)
             dO2 = dev_out(B, d * z)
             db.read_batch_masked_async(dR, B, dS, dO2)

@@ -14,7 +14,7 @@ from paper_2001_08250_gb300 import synth, talekpir
 
 pytestmark = pytest.mark.gpu
 
-PLAIN, BATCHED, PLAIN_REG, M4RM = 1, 2, 3, 4
+PLAIN, BATCHED, PLAIN_REG, M4RM, TENSOR = 1, 2, 3, 4, 5
 
 
 def _db(n, d, z, T):
@@ -33,7 +33,7 @@ EDGE = [
 
 
 @pytest.mark.parametrize("n,d,z,B", EDGE)
-@pytest.mark.parametrize("kernel", [PLAIN, BATCHED, PLAIN_REG, M4RM])
+@pytest.mark.parametrize("kernel", [PLAIN, BATCHED, PLAIN_REG, M4RM, TENSOR])
 def test_edge_shapes_bit_exact(n, d, z, B, kernel):
     require_cuda()
     T = synth.table_bytes(n, d, z, seed=21, table=n * 7 + d)
@@ -56,7 +56,7 @@ def test_empty_batch_and_zero_vector():
     T = synth.table_bytes(n, d, z, seed=3)
     with _db(n, d, z, T) as db:
         assert db.read_batch(np.zeros((0, 2), dtype=np.uint64)).shape == (0, d * z)
-        for k in (PLAIN, BATCHED, PLAIN_REG, M4RM):
+        for k in (PLAIN, BATCHED, PLAIN_REG, M4RM, TENSOR):
             db.set_kernel(k)
             assert not db.read_batch(np.zeros((6, 2), dtype=np.uint64)).any()
             # one-hot rows return exactly their bucket
@@ -115,7 +115,7 @@ def test_paper_scale_table_batches(paper_scale, B):
         check_rows(T, n, d, z, R, Out, sorted({0, B - 1, B // 2}))
         freivalds(T, n, d, z, R, Out, trials=12, seed=B)
         # forced kernels agree with the automatic choice
-        for k in (PLAIN, BATCHED, PLAIN_REG, M4RM):
+        for k in (PLAIN, BATCHED, PLAIN_REG, M4RM, TENSOR):
             db.set_kernel(k)
             dO2 = dev_out(B, d * z)
             db.read_batch_async(dR, B, dO2)
@@ -263,4 +263,27 @@ def test_multi_table_large_batches_four_russians_bit_exact():
     g.close()
     for db in dbs:
         db.close()
+    assert talekpir.device_status() == talekpir.OK
+
+
+@pytest.mark.parametrize("n,B", [(32768, 256), (40003, 129), (70001, 300), (65, 7),
+                                 (131075, 64)])
+def test_tensor_kernel_exact_counts_all_ones(n, B):
+    """All-ones requests against a table whose columns are set on every row,
+    on even rows, or on rows k = 0 mod 3: the tensor-core kernel's
+    accumulators reach the largest counts a k-chunk can hold (every bucket
+    selected), and the three column classes give both parities."""
+    require_cuda()
+    d, z = 1, 64
+    T = np.zeros((n, d * z), dtype=np.uint8)
+    T[:, 32:] = 0xFF
+    T[0::2, 16:32] = 0xFF
+    T[0::3, :16] = 0xA5
+    R = np.full((B, (n + 63) // 64), np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+    exp = oracle.read(T, n, d, z, R[0])
+    assert exp.any()
+    with _db(n, d, z, T) as db:
+        db.set_kernel(TENSOR)
+        got = db.read_batch(R)
+    assert (got == exp[None, :]).all()
     assert talekpir.device_status() == talekpir.OK

@@ -34,7 +34,7 @@ def _combine(parts, B, row):
 @pytest.mark.parametrize("n,d,z,B", [(4097, 2, 256, 40), (1000, 4, 1024, 260), (130, 1, 16, 3),
                                      (2049, 8, 512, 180)])
 @pytest.mark.parametrize("parts", [1, 2, 3, 5])
-@pytest.mark.parametrize("kernel", [0, 1, 2, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4, 5])
 def test_sharded_read_bit_exact(n, d, z, B, parts, kernel):
     require_cuda()
     T = synth.table_bytes(n, d, z, seed=92, table=n)
