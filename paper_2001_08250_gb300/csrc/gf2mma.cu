@@ -17,7 +17,8 @@
 //   warps 0-3   table producers: each takes 32 rows of a raw stage, one row
 //               per lane, and writes the row's 256 bits as e4m3 bytes (a set
 //               bit = 2^-6) into the B operand, which is MN-major (columns
-//               contiguous), so a table row needs no transposition;
+//               contiguous), so a table row needs no transposition (buckets
+//               and columns take the shared order of g_spread);
 //   warps 4-7   request producers: expand each request's 128 bits of the
 //               stage into the other operand (the next stage's words are
 //               loaded while the current one is expanded);
@@ -63,6 +64,14 @@ constexpr uint32_t kGTmemCols = 512;
 constexpr uint64_t kGWaitNs = 4000000000ull;
 constexpr uint32_t kGOne = 0x08u;                // e4m3 2^-6: the value of a set bit
 constexpr uint64_t kGMaxCount = 32768;           // largest count one accumulator holds
+
+// Descriptor increments (start address in 16-byte units): one stage, one
+// 128-row A tile, one K-step of A (two 16-byte K chunks), one K-step of B
+// (four 8-bucket K groups).
+constexpr uint64_t kDescStage = kGStageBytes >> 4;
+constexpr uint64_t kDescTile = kGTile >> 4;
+constexpr uint64_t kDescKa = (2 * kGLbo) >> 4;
+constexpr uint64_t kDescKb = (4 * kGLboB) >> 4;
 
 // Instruction descriptor: D fp32, A and B e4m3, A K-major, B MN-major (bit
 // 16), N = 256, M = 128.
@@ -146,16 +155,22 @@ __device__ __forceinline__ uint32_t g_off_b(uint32_t g, uint32_t k) {
   return g * kGSboB + (k >> 3) * kGLboB + (k & 7u) * 16u;
 }
 
-// Bits 4a..4a+3 of x as four e4m3 bytes (kGOne or 0): spreads the nibble to
-// bit 3 of each byte with one multiply (the four shifted copies never overlap).
-__device__ __forceinline__ uint32_t g_nib(uint32_t x, int a) {
-  static_assert(kGOne == 0x08u, "the multiply below lands each bit on bit 3 of its byte");
-  return (((x >> (4 * a)) & 0xFu) * 0x01020408u) & (kGOne * 0x01010101u);
+// Operand order within a K-step of 32 buckets (and within a word of 32 table
+// columns): byte 4m + j of the K-step (or of the 32 columns) holds bit m + 8j
+// of the word.  The product sums over K, so any order both operands share is
+// the same product; this one turns a word into its 32 e4m3 bytes (kGOne where
+// the bit is set) with one shift and one mask per 4 bytes.  The epilogue
+// undoes the column order when it packs the parities.
+__device__ __forceinline__ void g_spread(uint32_t x, uint4& lo, uint4& hi) {
+  static_assert(kGOne == 0x08u, "each bit lands on bit 3 of its byte");
+  constexpr uint32_t m = kGOne * 0x01010101u;
+  lo = make_uint4((x << 3) & m, (x << 2) & m, (x << 1) & m, x & m);
+  hi = make_uint4((x >> 1) & m, (x >> 2) & m, (x >> 3) & m, (x >> 4) & m);
 }
-// 16 bits (bits 16h..16h+15 of x) as one 16-byte chunk of operand bytes
-__device__ __forceinline__ uint4 g_chunk(uint32_t x, int h) {
-  return make_uint4(g_nib(x, 4 * h), g_nib(x, 4 * h + 1), g_nib(x, 4 * h + 2), g_nib(x, 4 * h + 3));
-}
+// Bucket (0..31 within its K-step) held by K position p of the K-step: the
+// table expanders read that row, so that each lane stores to K position p and
+// a warp's operand stores stay contiguous (bank-conflict free)
+__device__ __forceinline__ uint32_t g_kbucket(uint32_t p) { return (p >> 2) + 8u * (p & 3u); }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
@@ -223,14 +238,17 @@ __device__ __forceinline__ void g_red_xor64(uint32_t* p, uint32_t lo, uint32_t h
   asm volatile("red.relaxed.gpu.global.xor.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Parity word of 32 accumulator columns: each value is an exact count times
-// 2^-12; scaling by 2^12 and adding 2^23 puts the count in the mantissa, whose
-// lowest bit is the count's parity.
+// Parity word of the 32 accumulator columns of one table word: each value is
+// an exact count times 2^-12; scaling by 2^12 and adding 2^23 puts the count
+// in the mantissa, whose lowest bit is the count's parity.  Column v of the
+// word holds table bit 4 (v >> 4) + ((v >> 2) & 3) + 8 (v & 3) (the operand
+// order of g_spread).
 __device__ __forceinline__ uint32_t g_parity_word(const uint32_t (&r)[32]) {
   uint32_t w = 0;
 #pragma unroll
-  for (int j = 0; j < 32; ++j)
-    w |= (__float_as_uint(fmaf(__uint_as_float(r[j]), 4096.f, 8388608.f)) & 1u) << j;
+  for (int v = 0; v < 32; ++v)
+    w |= (__float_as_uint(fmaf(__uint_as_float(r[v]), 4096.f, 8388608.f)) & 1u)
+         << (4 * (v >> 4) + ((v >> 2) & 3) + 8 * (v & 3));
   return w;
 }
 
@@ -245,6 +263,37 @@ __device__ __forceinline__ void g_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One stage of the request operand: waits for the stage slot, writes this
+// thread's request in each M-tile (128 bits of the stage as e4m3 bytes,
+// K-major) and marks its part of the stage full.  False if the CTA aborted.
+__device__ __forceinline__ bool g_req_stage(const GLaunch& L, const GCursor& c,
+                                            const uint64_t (&x)[4], uint32_t iter, uint32_t q,
+                                            uint32_t stage0, uint64_t* full, uint64_t* empty,
+                                            volatile int* abort_flag, int* status) {
+  const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
+  if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) return false;
+  const uint32_t st = stage0 + s * kGStageBytes;
+#pragma unroll
+  for (uint32_t t = 0; t < 2; ++t) {
+    const uint32_t b = c.it.b0 + 128u * t + q;
+    if (t < c.it.mt && b < L.B) {
+      const uint32_t xw[4] = {static_cast<uint32_t>(x[2 * t]), static_cast<uint32_t>(x[2 * t] >> 32),
+                              static_cast<uint32_t>(x[2 * t + 1]), static_cast<uint32_t>(x[2 * t + 1] >> 32)};
+      const uint32_t abase = st + t * kGTile + g_off(q, 0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {  // K-step k: buckets ks + 32 k .. ks + 32 k + 31
+        uint4 lo, hi;
+        g_spread(xw[k], lo, hi);
+        st_shared_v4(abase + (2 * k) * kGLbo, lo);
+        st_shared_v4(abase + (2 * k + 1) * kGLbo, hi);
+      }
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mb::arrive(&full[s]);
+  return true;
 }
 
 __global__ void __launch_bounds__(kGThreads, 1)
@@ -323,18 +372,22 @@ __global__ void __launch_bounds__(kGThreads, 1)
       const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
       const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
       if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) break;
-      // row ks + 32 warp + lane of the strip (zeros past the table: TMA fill)
-      const uint32_t ra = raw0 + rs * kGRawBytes + (32u * warp + lane) * (kGWords * 4);
+      // row ks + 32 warp + g_kbucket(lane) of the strip (zeros past the table:
+      // TMA fill), stored at K position 32 warp + lane
+      const uint32_t ra = raw0 + rs * kGRawBytes + (32u * warp + g_kbucket(lane)) * (kGWords * 4);
       const uint4 a = ld_shared_v4(ra), b = ld_shared_v4(ra + 16);
       if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
       uint32_t used = 0;
       if (c.ks + 32u * warp < c.it.k1) {
         const uint32_t w[kGWords] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        const uint32_t o = stage0 + s * kGStageBytes + 2 * kGTile + g_off_b(0, 32u * warp + lane);
+        const uint32_t o =
+            stage0 + s * kGStageBytes + 2 * kGTile + g_off_b(0, 32u * warp + lane);
 #pragma unroll
-        for (int i = 0; i < kGWords; ++i) {
-          st_shared_v4(o + (2 * i) * kGSboB, g_chunk(w[i], 0));      // columns 32 i .. 32 i + 15
-          st_shared_v4(o + (2 * i + 1) * kGSboB, g_chunk(w[i], 1));  // columns 32 i + 16 .. 32 i + 31
+        for (int i = 0; i < kGWords; ++i) {  // word i: columns 32 i .. 32 i + 31
+          uint4 lo, hi;
+          g_spread(w[i], lo, hi);
+          st_shared_v4(o + (2 * i) * kGSboB, lo);
+          st_shared_v4(o + (2 * i + 1) * kGSboB, hi);
         }
       } else {
         used = a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
@@ -350,39 +403,37 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
   } else if (warp < 8) {
     // ------------------------ request expanders ------------------------
+    // Three register sets, each loaded three stages ahead of its use, so a
+    // stage never waits on the request words' (L2) latency.
     const uint32_t q = threadIdx.x - 128u;
+    GCursor ca = g_cur_start(L);
+    GCursor cb = ca;
+    g_cur_next(cb, L);
+    GCursor cc = cb;
+    g_cur_next(cc, L);
+    uint64_t xa[4], xb[4], xc[4];
+    g_req_load(L, ca, q, xa);
+    g_req_load(L, cb, q, xb);
+    g_req_load(L, cc, q, xc);
     uint32_t iter = 0;
-    GCursor c = g_cur_start(L);
-    uint64_t nx[4];
-    g_req_load(L, c, q, nx);
-    while (c.valid) {
-      const uint64_t x[4] = {nx[0], nx[1], nx[2], nx[3]};
-      GCursor nc = c;
-      g_cur_next(nc, L);
-      g_req_load(L, nc, q, nx);  // the next stage's words, in flight meanwhile
-      const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
-      if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
-      const uint32_t st = stage0 + s * kGStageBytes;
-#pragma unroll
-      for (uint32_t t = 0; t < 2; ++t) {
-        const uint32_t b = c.it.b0 + 128u * t + q;
-        if (t < c.it.mt && b < L.B) {
-          const uint32_t xw[4] = {static_cast<uint32_t>(x[2 * t]), static_cast<uint32_t>(x[2 * t] >> 32),
-                                  static_cast<uint32_t>(x[2 * t + 1]),
-                                  static_cast<uint32_t>(x[2 * t + 1] >> 32)};
-          const uint32_t abase = st + t * kGTile;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) st_shared_v4(abase + g_off(q, 16u * k), g_chunk(xw[k >> 1], k & 1));
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mb::arrive(&full[s]);
-      c = nc;
-      ++iter;
+    for (;;) {
+      if (!ca.valid || !g_req_stage(L, ca, xa, iter++, q, stage0, full, empty, abort_flag, status)) break;
+      ca = cc;
+      g_cur_next(ca, L);
+      g_req_load(L, ca, q, xa);
+      if (!cb.valid || !g_req_stage(L, cb, xb, iter++, q, stage0, full, empty, abort_flag, status)) break;
+      cb = ca;
+      g_cur_next(cb, L);
+      g_req_load(L, cb, q, xb);
+      if (!cc.valid || !g_req_stage(L, cc, xc, iter++, q, stage0, full, empty, abort_flag, status)) break;
+      cc = cb;
+      g_cur_next(cc, L);
+      g_req_load(L, cc, q, xc);
     }
   } else {
     // ------------------------- MMA issue + epilogue -------------------------
     const uint32_t ew = warp - 8;  // tensor-memory lanes 32 ew .. 32 ew + 31
+    const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc_b(stage0 + 2 * kGTile);
     const uint32_t lag = L.nbuf - 1;
     uint32_t iter = 0;
     bool pdl_waited = false;
@@ -404,13 +455,28 @@ __global__ void __launch_bounds__(kGThreads, 1)
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = stage0 + s * kGStageBytes;
+            // descriptors: the stage's bases plus constant K-step offsets (a
+            // single issuing thread is latency-bound: building descriptors
+            // from addresses before every MMA halved the tensor pipe's rate)
+            const uint64_t sa = adesc0 + s * kDescStage, sb = bdesc0 + s * kDescStage;
+            const uint32_t acc0 = ks > it.k0 ? 1u : 0u;
             const uint64_t left = it.k1 - ks;
-            const uint32_t nk = left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
-            for (uint32_t j = 0; j < nk; ++j)
-              for (uint32_t t = 0; t < it.mt; ++t)
-                g_mma(acc + 256u * t, g_desc(st + t * kGTile + 2u * kGLbo * j),
-                      g_desc_b(st + 2 * kGTile + 4u * kGLboB * j), (ks > it.k0 || j > 0) ? 1u : 0u);
+            if (left >= kGKStage && it.mt == 2) {
+#pragma unroll
+              for (uint32_t j = 0; j < 4; ++j) {
+                g_mma(acc, sa + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+                g_mma(acc + 256u, sa + kDescTile + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+              }
+            } else if (left >= kGKStage) {
+#pragma unroll
+              for (uint32_t j = 0; j < 4; ++j) g_mma(acc, sa + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+            } else {
+              const uint32_t nk = static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
+              for (uint32_t j = 0; j < nk; ++j)
+                for (uint32_t t = 0; t < it.mt; ++t)
+                  g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j,
+                        j ? 1u : acc0);
+            }
             g_commit(&empty[s]);
           }
           if (ok) g_commit(&accf[buf]);
