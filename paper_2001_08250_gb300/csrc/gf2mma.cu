@@ -62,6 +62,7 @@ constexpr int kGRawBytes = 128 * kGWords * 4;    // 128 rows x 8 words: 4 KiB
 constexpr int kGSmem = 1024 + kGStages * kGStageBytes + kGRaw * kGRawBytes;
 constexpr uint32_t kGTmemCols = 512;
 constexpr uint64_t kGWaitNs = 4000000000ull;
+constexpr int kGIssuers = 1;                     // MMA-issuing threads
 constexpr uint32_t kGOne = 0x08u;                // e4m3 2^-6: the value of a set bit
 constexpr uint64_t kGMaxCount = 32768;           // largest count one accumulator holds
 
@@ -315,13 +316,13 @@ __global__ void __launch_bounds__(kGThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kGStages; ++s) {
       mb::init(&full[s], 256);
-      mb::init(&empty[s], 1);
+      mb::init(&empty[s], kGIssuers);
     }
     for (int b = 0; b < 2; ++b) {
-      mb::init(&accf[b], 1);
+      mb::init(&accf[b], kGIssuers);
       mb::init(&acce[b], 128);
     }
-    mb::init(&drain, 1);
+    mb::init(&drain, kGIssuers);
     for (int s = 0; s < kGRaw; ++s) {
       mb::init(&raw_full[s], 1);
       mb::init(&raw_empty[s], 4);
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const uint32_t ew = warp - 8;  // tensor-memory lanes 32 ew .. 32 ew + 31
     const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc_b(stage0 + 2 * kGTile);
     const uint32_t lag = L.nbuf - 1;
-    uint32_t iter = 0;
+    uint32_t iter = 0, is = 0, iph = 0;  // issuer: stage count, slot, phase
     bool pdl_waited = false;
     for (uint32_t r = 0;; ++r) {
       const uint32_t item = blockIdx.x + r * gridDim.x;
@@ -449,8 +450,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
           if (r >= L.nbuf)
             ok = mb::wait_sleep(&acce[buf], ((r / L.nbuf) - 1u) & 1u, abort_flag, status, kGWaitNs, 64);
           for (uint64_t ks = it.k0; ok && ks < it.k1; ks += kGKStage, ++iter) {
-            const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
-            if (!mb::wait(&full[s], ph, abort_flag, status, kGWaitNs)) {
+            // stage slot and phase of iteration iter, kept incrementally
+            const uint32_t s = is, ph = iph;
+            if (++is == kGStages) {
+              is = 0;
+              iph ^= 1u;
+            }
+            // the stage is normally full already: a plain test first, the
+            // bounded wait only when it is not
+            if (!mb::test(&full[s], ph) && !mb::wait(&full[s], ph, abort_flag, status, kGWaitNs)) {
               ok = false;
               break;
             }
