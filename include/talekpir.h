@@ -225,11 +225,12 @@ tpir_status tpir_tune_clear(void);
 
 /* Many tables in ONE persistent launch per kernel kind (the uneven-batching
  * workload): job i reads B_i rows of d_req_bits_i against db_i into d_out_i.
- * Tables may differ in n, d and msg_bytes.  Jobs of >= 176 requests on rows
- * of >= 256 bytes go to the Four-Russians kernel (one launch for jobs of up
- * to 256 requests, one for larger ones), the others to one launch of the
- * register-tiled kernel; every launch claims its items dynamically.  A job
- * with d_seeds (B x 32 bytes, 16-byte aligned) is masked as in
+ * Tables may differ in n, d and msg_bytes.  Jobs of >= 96 requests on rows of
+ * >= 256 bytes share one launch of the tensor-core kernel, the others one
+ * launch of the register-tiled kernel (a db forced to kernel 4 sends its jobs
+ * to the Four-Russians kernel instead: one launch for jobs of up to 256
+ * requests, one for larger ones; forced to 2, to the register-tiled one).  A
+ * job with d_seeds (B x 32 bytes, 16-byte aligned) is masked as in
  * tpir_read_batch_masked_async; NULL = plain replies.  Up to TPIR_MAX_JOBS
  * jobs per call. */
 #define TPIR_MAX_JOBS 128

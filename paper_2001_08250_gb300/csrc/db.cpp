@@ -270,10 +270,11 @@ tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, 
 }
 
 tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st) {
-  // large batches on rows of >= 256 bytes: persistent Four-Russians launches
-  // (512-request tiles above 256 requests, else 256); the rest: one
+  // large batches on rows of >= 256 bytes: one launch of the tensor-core
+  // kernel (a db forced to the Four-Russians kernel: its launches, 512-request
+  // tiles above 256 requests, else 256); the rest, and dbs forced to it: one
   // persistent launch of the register-tiled kernel
-  std::vector<M4Request> m4, m4w;
+  std::vector<M4Request> tc, m4, m4w;
   std::vector<tpir_read_job> lop3;
   for (uint32_t i = 0; i < njobs; ++i) {
     const tpir_read_job& q = jobs[i];
@@ -286,12 +287,17 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
                       q.d_req_bits + q.db->req_off, q.db->words64, q.B,
                       reinterpret_cast<uint32_t*>(q.d_out),
                       static_cast<const uint8_t*>(q.d_seeds)};
-    if (q.B >= kM4rmMinB && q.db->Wd >= 64)
+    const int forced = q.db->forced_kernel;
+    if (forced == 4 && q.db->Wd >= 64)
       (q.B > 256 ? m4w : m4).push_back(r);
+    else if (forced == 5 || (forced == 0 && q.B >= kTensorMinB && q.db->Wd >= 64))
+      tc.push_back(r);
     else
       lop3.push_back(q);
   }
   tpir_status s = enqueue_multi_lop3(lop3.data(), static_cast<uint32_t>(lop3.size()), st);
+  if (s == TPIR_OK && !tc.empty())
+    s = cuda_status(launch_gf2_mma_multi(tc.data(), static_cast<uint32_t>(tc.size()), st));
   if (s == TPIR_OK && !m4w.empty())
     s = cuda_status(launch_m4rm_multi(m4w.data(), static_cast<uint32_t>(m4w.size()), true, st));
   if (s == TPIR_OK && !m4.empty())

@@ -37,9 +37,11 @@
 
 #include <algorithm>
 #include <map>
+#include <vector>
 #include <mutex>
 #include <tuple>
 
+#include "chacha.cuh"
 #include "mbar.cuh"
 #include "tpir_internal.h"
 
@@ -78,32 +80,67 @@ constexpr uint64_t kDescKb = (4 * kGLboB) >> 4;
 // 16), N = 256, M = 128.
 constexpr uint32_t kGIdesc = (1u << 4) | (1u << 16) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
-struct GLaunch {
-  const uint32_t* T;
+// One table's read in a launch (one job of a many-table launch).
+struct GJob {
   const uint64_t* R;
   uint32_t* out;
+  const uint8_t* seeds;  // masks of a serialized-PIR read, or null
   uint64_t n;
   uint32_t Wd, words64, B;
-  uint32_t n_strips, n_mb, kc_rows, total_items;
-  uint32_t split, nbuf;
+  uint32_t n_strips, n_mb, kc_rows;
+  uint32_t item_begin;   // index of this job's first item in the launch
+  uint32_t split;        // replies are initialised first and XOR-reduced into
 };
 
+// A launch: NJ jobs (one for a single-table read), each with the tensor map of
+// its table, in the kernel parameters.
+template <int NJ>
+struct GLaunch {
+  CUtensorMap maps[NJ];
+  GJob jobs[NJ];
+  uint32_t njobs, total_items, nbuf, pad;
+};
+static_assert(sizeof(GLaunch<TPIR_MAX_JOBS>) <= 32000, "kernel parameters must stay below 32 KB");
+
 struct GItem {
-  uint32_t strip, b0, mt;
+  uint32_t job, strip, b0, mt;
   uint64_t k0, k1;
 };
 
-__device__ __forceinline__ GItem g_decode(const GLaunch& L, uint32_t item) {
+template <int NJ>
+__device__ __forceinline__ GItem g_decode(const GLaunch<NJ>& L, uint32_t item) {
+  uint32_t lo = 0;
+  if constexpr (NJ > 1) {
+    uint32_t hi = L.njobs - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (L.jobs[mid].item_begin <= item)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+  }
+  const GJob& J = L.jobs[lo];
   GItem it;
-  it.strip = item % L.n_strips;
-  const uint32_t rest = item / L.n_strips;
-  const uint32_t mb = rest % L.n_mb;
-  it.k0 = static_cast<uint64_t>(rest / L.n_mb) * L.kc_rows;
-  it.k1 = min(L.n, it.k0 + L.kc_rows);
+  it.job = lo;
+  const uint32_t local = item - J.item_begin;
+  it.strip = local % J.n_strips;
+  const uint32_t rest = local / J.n_strips;
+  const uint32_t mb = rest % J.n_mb;
+  it.k0 = static_cast<uint64_t>(rest / J.n_mb) * J.kc_rows;
+  it.k1 = min(J.n, it.k0 + J.kc_rows);
   it.b0 = mb * 256u;
-  const uint32_t left = L.B - it.b0;
+  const uint32_t left = J.B - it.b0;
   it.mt = left > 128u ? 2u : 1u;
   return it;
+}
+
+// The r-th item of this CTA.  Items are listed by descending cost; the CTAs
+// take them round by round, sweeping the grid in alternate directions so that
+// no CTA takes the largest item of every round.
+__device__ __forceinline__ uint32_t g_item_of(uint32_t r) {
+  const uint32_t c = (r & 1u) ? gridDim.x - 1u - blockIdx.x : blockIdx.x;
+  return c + r * gridDim.x;
 }
 
 // Position in this CTA's sequence of stages (item r, stage start ks); every
@@ -114,21 +151,24 @@ struct GCursor {
   GItem it;
   bool valid;
 };
-__device__ __forceinline__ void g_cur_item(GCursor& c, const GLaunch& L) {
-  const uint32_t item = blockIdx.x + c.r * gridDim.x;
+template <int NJ>
+__device__ __forceinline__ void g_cur_item(GCursor& c, const GLaunch<NJ>& L) {
+  const uint32_t item = g_item_of(c.r);
   c.valid = item < L.total_items;
   if (c.valid) {
     c.it = g_decode(L, item);
     c.ks = c.it.k0;
   }
 }
-__device__ __forceinline__ GCursor g_cur_start(const GLaunch& L) {
+template <int NJ>
+__device__ __forceinline__ GCursor g_cur_start(const GLaunch<NJ>& L) {
   GCursor c;
   c.r = 0;
   g_cur_item(c, L);
   return c;
 }
-__device__ __forceinline__ void g_cur_next(GCursor& c, const GLaunch& L) {
+template <int NJ>
+__device__ __forceinline__ void g_cur_next(GCursor& c, const GLaunch<NJ>& L) {
   c.ks += kGKStage;
   if (c.ks >= c.it.k1) {
     ++c.r;
@@ -204,17 +244,21 @@ __device__ __forceinline__ void g_tma_load(uint32_t dst, const CUtensorMap* map,
 
 // the request words of one stage: this thread's request in each M-tile,
 // buckets ks .. ks + 127 (zeros past the request rows and the batch)
-__device__ __forceinline__ void g_req_load(const GLaunch& L, const GCursor& c, uint32_t q,
+template <int NJ>
+__device__ __forceinline__ void g_req_load(const GLaunch<NJ>& L, const GCursor& c, uint32_t q,
                                            uint64_t (&x)[4]) {
   const uint64_t wi = c.ks >> 6;
 #pragma unroll
+  for (uint32_t t = 0; t < 2; ++t) x[2 * t] = x[2 * t + 1] = 0ull;
+  if (!c.valid) return;
+  const GJob& J = L.jobs[c.it.job];
+#pragma unroll
   for (uint32_t t = 0; t < 2; ++t) {
     const uint32_t b = c.it.b0 + 128u * t + q;
-    x[2 * t] = x[2 * t + 1] = 0ull;
-    if (c.valid && t < c.it.mt && b < L.B) {
-      const uint64_t* rq = L.R + static_cast<uint64_t>(b) * L.words64;
+    if (t < c.it.mt && b < J.B) {
+      const uint64_t* rq = J.R + static_cast<uint64_t>(b) * J.words64;
       x[2 * t] = __ldg(rq + wi);
-      if (wi + 1 < L.words64) x[2 * t + 1] = __ldg(rq + wi + 1);
+      if (wi + 1 < J.words64) x[2 * t + 1] = __ldg(rq + wi + 1);
     }
   }
 }
@@ -269,7 +313,8 @@ __device__ __forceinline__ void g_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // One stage of the request operand: waits for the stage slot, writes this
 // thread's request in each M-tile (128 bits of the stage as e4m3 bytes,
 // K-major) and marks its part of the stage full.  False if the CTA aborted.
-__device__ __forceinline__ bool g_req_stage(const GLaunch& L, const GCursor& c,
+template <int NJ>
+__device__ __forceinline__ bool g_req_stage(const GLaunch<NJ>& L, const GCursor& c,
                                             const uint64_t (&x)[4], uint32_t iter, uint32_t q,
                                             uint32_t stage0, uint64_t* full, uint64_t* empty,
                                             volatile int* abort_flag, int* status) {
@@ -279,7 +324,7 @@ __device__ __forceinline__ bool g_req_stage(const GLaunch& L, const GCursor& c,
 #pragma unroll
   for (uint32_t t = 0; t < 2; ++t) {
     const uint32_t b = c.it.b0 + 128u * t + q;
-    if (t < c.it.mt && b < L.B) {
+    if (t < c.it.mt && b < L.jobs[c.it.job].B) {
       const uint32_t xw[4] = {static_cast<uint32_t>(x[2 * t]), static_cast<uint32_t>(x[2 * t] >> 32),
                               static_cast<uint32_t>(x[2 * t + 1]), static_cast<uint32_t>(x[2 * t + 1] >> 32)};
       const uint32_t abase = st + t * kGTile + g_off(q, 0);
@@ -297,9 +342,9 @@ __device__ __forceinline__ bool g_req_stage(const GLaunch& L, const GCursor& c,
   return true;
 }
 
+template <int NJ>
 __global__ void __launch_bounds__(kGThreads, 1)
-    gf2_mma_kernel(const __grid_constant__ GLaunch L, const __grid_constant__ CUtensorMap tmap,
-                   int* status) {
+    gf2_mma_kernel(const __grid_constant__ GLaunch<NJ> L, int* status) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], accf[2], acce[2], drain;
   __shared__ __align__(8) uint64_t raw_full[kGRaw], raw_empty[kGRaw];
@@ -349,7 +394,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++p) {
         const uint32_t rs = p % kGRaw, ph = (p / kGRaw) & 1u;
         if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
-        g_tma_load(raw0 + rs * kGRawBytes, &tmap, static_cast<int>(c.it.strip * kGWords),
+        g_tma_load(raw0 + rs * kGRawBytes, &L.maps[c.it.job], static_cast<int>(c.it.strip * kGWords),
                    static_cast<int>(c.ks), &raw_full[rs], kGRawBytes);
       }
       // Loads still landing (an aborted run) complete before the CTA exits: a
@@ -439,7 +484,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     uint32_t iter = 0, is = 0, iph = 0;  // issuer: stage count, slot, phase
     bool pdl_waited = false;
     for (uint32_t r = 0;; ++r) {
-      const uint32_t item = blockIdx.x + r * gridDim.x;
+      const uint32_t item = g_item_of(r);
       const bool issue = item < L.total_items;
       if (warp == 8) {
         if (issue && lane == 0 && !*abort_flag) {
@@ -497,7 +542,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       }
       // epilogue of item e
       const uint32_t e = r - lag;
-      const uint32_t eitem = blockIdx.x + e * gridDim.x;
+      const uint32_t eitem = g_item_of(e);
       if (eitem >= L.total_items || *abort_flag) break;
       const GItem it = g_decode(L, eitem);
       const uint32_t buf = L.nbuf == 2 ? (e & 1u) : 0u;
@@ -507,6 +552,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         asm volatile("griddepcontrol.wait;" ::: "memory");  // replies initialised / released
         pdl_waited = true;
       }
+      const GJob& J = L.jobs[it.job];
       const uint32_t w0 = it.strip * kGWords;
       for (uint32_t t = 0; t < it.mt; ++t) {
         const uint32_t b = it.b0 + 128u * t + 32u * ew + lane;
@@ -514,29 +560,29 @@ __global__ void __launch_bounds__(kGThreads, 1)
 #pragma unroll
         for (int c = 0; c < kGWords; ++c) {
           pw[c] = 0u;
-          if (w0 + c < L.Wd) {  // uniform across the warp
+          if (w0 + c < J.Wd) {  // uniform across the warp
             uint32_t v[32];
             g_ld32(tmem + buf * 256u + 256u * t + 32u * c + ((32u * ew) << 16), v);
             pw[c] = g_parity_word(v);
           }
         }
-        if (b < L.B) {
-          uint32_t* o = L.out + static_cast<uint64_t>(b) * L.Wd + w0;
-          if (L.split) {
+        if (b < J.B) {
+          uint32_t* o = J.out + static_cast<uint64_t>(b) * J.Wd + w0;
+          if (J.split) {
 #pragma unroll
             for (int c = 0; c < kGWords; c += 2) {
-              if (w0 + c + 1 < L.Wd)
+              if (w0 + c + 1 < J.Wd)
                 g_red_xor64(o + c, pw[c], pw[c + 1]);
-              else if (w0 + c < L.Wd)
+              else if (w0 + c < J.Wd)
                 atomicXor(o + c, pw[c]);
             }
-          } else if (w0 + kGWords <= L.Wd) {
+          } else if (w0 + kGWords <= J.Wd) {
             reinterpret_cast<uint4*>(o)[0] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
             reinterpret_cast<uint4*>(o)[1] = make_uint4(pw[4], pw[5], pw[6], pw[7]);
           } else {
 #pragma unroll
             for (int c = 0; c < kGWords; ++c)
-              if (w0 + c < L.Wd) o[c] = pw[c];
+              if (w0 + c < J.Wd) o[c] = pw[c];
           }
         }
       }
@@ -603,72 +649,160 @@ cudaError_t g_table_map(const uint32_t* T, uint64_t n, uint32_t Wd, CUtensorMap*
   return cudaSuccess;
 }
 
+// Initialises the replies of the jobs that XOR-reduce into them (zeros, or
+// the masks of a masked job) before the scan: grid.y = job.  PDL-chained like
+// the scan, it waits for the previous kernel before writing.
+template <int NJ>
+__global__ void gf2_init_kernel(const __grid_constant__ GLaunch<NJ> L) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const GJob& J = L.jobs[blockIdx.y];
+  if (!J.split) return;
+  init_replies(reinterpret_cast<uint4*>(J.out), J.B, J.Wd / 4, J.seeds,
+               blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+}
+
+// Job fields that do not depend on the k-chunking.
+GJob g_job(const uint64_t* R, uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+           uint64_t n, uint32_t Wd) {
+  GJob j{};
+  j.R = R;
+  j.out = out;
+  j.seeds = seeds;
+  j.n = n;
+  j.Wd = Wd;
+  j.words64 = words64;
+  j.B = B;
+  j.n_strips = (Wd + kGWords - 1) / kGWords;
+  j.n_mb = (B + 255) / 256;
+  return j;
+}
+
+// k-chunks of kc_rows buckets: a multiple of a stage, at most kGMaxCount (a
+// k-chunk's counts stay in the range in which the fp32 accumulators were
+// checked exact, whatever the tensor cores' internal accumulation width)
+uint32_t g_clamp_rows(uint64_t rows, uint64_t n) {
+  rows = std::max<uint64_t>(rows, kGKStage);
+  rows = (rows + kGKStage - 1) / kGKStage * kGKStage;
+  rows = std::min<uint64_t>(rows, (n + kGKStage - 1) / kGKStage * kGKStage);
+  return static_cast<uint32_t>(std::min<uint64_t>(rows, kGMaxCount));
+}
+
+template <int NJ>
+cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
+  static bool ready = false;
+  if (!ready) {
+    cudaError_t e = cudaFuncSetAttribute(gf2_mma_kernel<NJ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+    if (e != cudaSuccess) return e;
+    ready = true;
+  }
+  int* status = device_status_word();
+  if (!status) return cudaErrorInvalidSymbol;
+  bool any = false;
+  for (uint32_t i = 0; i < L.njobs; ++i) any |= L.jobs[i].split != 0;
+  cudaError_t e = cudaSuccess;
+  if (any) e = launch_pdl(gf2_init_kernel<NJ>, dim3(64, L.njobs), dim3(256), 0, st, L);
+  if (e != cudaSuccess) return e;
+  const uint32_t grid = std::min<uint32_t>(L.total_items, device_sm_count());
+  return launch_pdl(gf2_mma_kernel<NJ>, dim3(grid), dim3(kGThreads), kGSmem, st, L, status);
+}
+
 }  // namespace
 
 cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
                            uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                            cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  int* status = device_status_word();
-  if (!status) return cudaErrorInvalidSymbol;
-  static bool ready = false;
-  if (!ready) {
-    cudaError_t e = cudaFuncSetAttribute(gf2_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGSmem);
-    if (e != cudaSuccess) return e;
-    ready = true;
-  }
-  GLaunch L{};
-  L.T = T;
-  L.R = R;
-  L.out = out;
-  L.n = n;
-  L.Wd = Wd;
-  L.words64 = words64;
-  L.B = B;
-  L.n_strips = (Wd + kGWords - 1) / kGWords;
-  L.n_mb = (B + 255) / 256;
+  GLaunch<1> L{};
+  L.njobs = 1;
+  GJob J = g_job(R, words64, B, out, seeds, n, Wd);
   L.nbuf = B <= 128 ? 2u : 1u;
   const int grid = device_sm_count();
-  // k-chunks (multiples of a stage) minimising rounds x item time on the grid;
-  // item time ~ MMAs (147 cycles each at N = 256, K = 32) + epilogue, which the
-  // second accumulator hides when an item holds one M-tile
+  // k-chunks minimising rounds x item time on the grid; item time ~ MMAs
+  // (128 cycles each at N = 256, K = 32) + epilogue, which the second
+  // accumulator hides when an item holds one M-tile
   const double mts = B <= 128 ? 1.0 : 2.0;
   const double epi = L.nbuf == 2 ? 600.0 : 2500.0;
-  // (a k-chunk's counts stay below kGMaxCount, the range in which the fp32
-  // accumulators were checked exact, whatever the tensor cores' internal
-  // accumulation width)
   const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
   const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
   double best = 1e300;
   uint64_t best_rows = kGKStage;
   for (uint64_t c = std::max<uint64_t>(1, min_kc); c <= std::max<uint64_t>(min_kc, std::min<uint64_t>(max_kc, 512)); ++c) {
-    uint64_t rows = (n + c - 1) / c;
-    rows = (rows + kGKStage - 1) / kGKStage * kGKStage;
-    if (rows > kGMaxCount) continue;
+    const uint64_t rows = g_clamp_rows((n + c - 1) / c, n);
     const uint64_t kcs = (n + rows - 1) / rows;
-    const uint64_t items = static_cast<uint64_t>(L.n_strips) * L.n_mb * kcs;
+    const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
     const uint64_t rounds = (items + grid - 1) / grid;
     const double cost = static_cast<double>(rounds) *
-                        (static_cast<double>(rows) / kGKStep * mts * 147.0 + epi);
+                        (static_cast<double>(rows) / kGKStep * mts * 128.0 + epi);
     if (cost < best) {
       best = cost;
       best_rows = rows;
     }
   }
-  L.kc_rows = static_cast<uint32_t>(std::min<uint64_t>(best_rows, 0x7FFFFF80ull));
-  const uint64_t kcs = (n + L.kc_rows - 1) / L.kc_rows;
-  const uint64_t items = static_cast<uint64_t>(L.n_strips) * L.n_mb * kcs;
+  J.kc_rows = static_cast<uint32_t>(best_rows);
+  const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;
+  const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
   if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  J.item_begin = 0;
+  J.split = (kcs > 1 || seeds) ? 1u : 0u;
+  L.jobs[0] = J;
   L.total_items = static_cast<uint32_t>(items);
-  L.split = (kcs > 1 || seeds) ? 1u : 0u;
-  CUtensorMap tmap;
-  cudaError_t e = g_table_map(T, n, Wd, &tmap);
+  cudaError_t e = g_table_map(T, n, Wd, &L.maps[0]);
   if (e != cudaSuccess) return e;
-  if (L.split) e = launch_init_replies(reinterpret_cast<uint4*>(out), B, Wd / 4, seeds, st);
-  if (e != cudaSuccess) return e;
-  return launch_pdl(gf2_mma_kernel, dim3(static_cast<uint32_t>(std::min<uint64_t>(items, grid))),
-                    dim3(kGThreads), kGSmem, st, L, tmap, status);
+  return g_launch<1>(L, st);
+}
+
+cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  if (count > TPIR_MAX_JOBS) return cudaErrorInvalidValue;
+  const int grid = device_sm_count();
+  // items of about equal cost (bucket rows x M-tiles), ~8 per CTA; jobs in
+  // descending item cost, assigned round-robin to the CTAs
+  std::vector<GJob> js;
+  std::vector<const M4Request*> src;
+  bool all_small = true;
+  double total = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const M4Request& q = reqs[i];
+    if (q.B == 0) continue;
+    GJob j = g_job(q.R, q.words64, q.B, q.out, q.seeds, q.n, q.Wd);
+    all_small &= q.B <= 128;
+    total += static_cast<double>(j.n_strips) * static_cast<double>(q.n) *
+             static_cast<double>((q.B + 127) / 128);
+    js.push_back(j);
+    src.push_back(&q);
+  }
+  if (js.empty()) return cudaSuccess;
+  const double target = total / (static_cast<double>(grid) * 8.0);
+  std::vector<double> cost(js.size());
+  for (size_t i = 0; i < js.size(); ++i) {
+    GJob& j = js[i];
+    const double mt = j.B > 128 ? 2.0 : 1.0;
+    j.kc_rows = g_clamp_rows(static_cast<uint64_t>(target / mt), j.n);
+    const uint64_t kcs = (j.n + j.kc_rows - 1) / j.kc_rows;
+    j.split = (kcs > 1 || j.seeds) ? 1u : 0u;
+    cost[i] = static_cast<double>(std::min<uint64_t>(j.kc_rows, j.n)) * mt;
+  }
+  std::vector<size_t> order(js.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+  GLaunch<TPIR_MAX_JOBS> L{};
+  L.njobs = 0;
+  L.nbuf = all_small ? 2u : 1u;
+  uint64_t items = 0;
+  for (size_t oi : order) {
+    GJob j = js[oi];
+    const uint64_t kcs = (j.n + j.kc_rows - 1) / j.kc_rows;
+    j.item_begin = static_cast<uint32_t>(items);
+    items += static_cast<uint64_t>(j.n_strips) * j.n_mb * kcs;
+    if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+    cudaError_t e = g_table_map(src[oi]->T, j.n, j.Wd, &L.maps[L.njobs]);
+    if (e != cudaSuccess) return e;
+    L.jobs[L.njobs++] = j;
+  }
+  L.total_items = static_cast<uint32_t>(items);
+  return g_launch<TPIR_MAX_JOBS>(L, st);
 }
 
 }  // namespace tpir

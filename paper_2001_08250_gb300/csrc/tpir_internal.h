@@ -125,6 +125,9 @@ cudaError_t launch_init_replies(uint4* out, uint32_t B, uint32_t row_u4, const u
 cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
                            uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                            cudaStream_t st);
+struct M4Request;
+// Many tables in one launch of the tensor-core kernel (up to TPIR_MAX_JOBS).
+cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st);
 int device_sm_count();
 int plain_ctas_per_sm();
 int batched_ctas_per_sm();

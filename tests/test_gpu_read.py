@@ -236,13 +236,15 @@ def test_autotuned_shape_stays_bit_exact():
     talekpir.tune_clear()
 
 
-def test_multi_table_large_batches_four_russians_bit_exact():
-    """Many tables with large batches: those on rows of >= 256 bytes share one
-    persistent Four-Russians launch (B-tiles of 256), the narrow one goes to
-    the register-tiled kernel; all bit-exact."""
+def test_multi_table_large_batches_bit_exact():
+    """Many tables with large batches in one call: those on rows of >= 256
+    bytes share one launch of the tensor-core kernel (and, with their dbs
+    forced to kernel 4, the Four-Russians kernel's 256- and 512-request
+    launches), the narrow one goes to the register-tiled kernel; all
+    bit-exact, directly and replayed from a captured graph."""
     require_cuda()
     shapes = [(1100, 2, 256, 200), (3000, 4, 1024, 256), (513, 8, 4096, 400), (700, 1, 64, 180),
-              (2049, 2, 512, 333)]
+              (2049, 2, 512, 333), (4096, 4, 1024, 96), (300, 2, 512, 128)]
     dbs, jobs, exp = [], [], []
     for i, (n, d, z, B) in enumerate(shapes):
         T = synth.table_bytes(n, d, z, seed=80, table=i)
@@ -251,16 +253,21 @@ def test_multi_table_large_batches_four_russians_bit_exact():
         dbs.append(db)
         jobs.append((db, B, to_dev(R), dev_out(B, d * z)))
         exp.append(oracle.read_batch(T, n, d, z, R))
-    talekpir.read_multi_async(jobs)
-    for (db, B, dR, dO), e in zip(jobs, exp):
-        assert np.array_equal(to_host(dO), e)
-    g = talekpir.MultiGraph(jobs)
-    for (_, _, _, dO) in jobs:
-        dO.zero_()
-    g.launch()
-    for (db, B, dR, dO), e in zip(jobs, exp):
-        assert np.array_equal(to_host(dO), e)
-    g.close()
+    for forced in (0, M4RM, TENSOR):
+        for db in dbs:
+            db.set_kernel(forced)
+        for (_, _, _, dO) in jobs:
+            dO.zero_()
+        talekpir.read_multi_async(jobs)
+        for (db, B, dR, dO), e in zip(jobs, exp):
+            assert np.array_equal(to_host(dO), e), forced
+        g = talekpir.MultiGraph(jobs)
+        for (_, _, _, dO) in jobs:
+            dO.fill_(0x5A)
+        g.launch()
+        for (db, B, dR, dO), e in zip(jobs, exp):
+            assert np.array_equal(to_host(dO), e), forced
+        g.close()
     for db in dbs:
         db.close()
     assert talekpir.device_status() == talekpir.OK
