@@ -59,6 +59,12 @@ def lib():
         L.oracle_mask.restype = None
         L.oracle_read_batch_masked.argtypes = [_vp, _u64, _u32, _u32, _vp, _u32, _vp, _vp]
         L.oracle_read_batch_masked.restype = None
+        L.oracle_rice_param.argtypes = [_u64, _u64]
+        L.oracle_rice_param.restype = _u32
+        L.oracle_rice_encode.argtypes = [_vp, _u64, _u32, _vp, _u64, _u64p]
+        L.oracle_rice_encode.restype = _u64
+        L.oracle_rice_decode.argtypes = [_vp, _u64, _u32, _u64, _u64, _vp]
+        L.oracle_rice_decode.restype = ctypes.c_int
         L.oracle_cuckoo_create.argtypes = [_u64, _u32, _u32, _u64, _u32, _u64]
         L.oracle_cuckoo_create.restype = _vp
         L.oracle_cuckoo_destroy.argtypes = [_vp]
@@ -148,6 +154,39 @@ def read_batch_masked(T: np.ndarray, n: int, d: int, z: int, R: np.ndarray,
     seeds = np.ascontiguousarray(seeds, dtype=np.uint8).reshape(B, 32)
     out = np.empty((B, d * z), dtype=np.uint8)
     lib().oracle_read_batch_masked(_ptr(T), n, d, z, _ptr(R), B, _ptr(seeds), _ptr(out))
+    return out
+
+
+def rice_param(m: int, count: int) -> int:
+    return int(lib().oracle_rice_param(m, count))
+
+
+def rice_encode(bits: np.ndarray, m: int, k: int | None = None):
+    """Rice code of the set bits of an m-bit vector: (stream bytes, nbits,
+    count, k); k defaults to rice_param(m, popcount)."""
+    b = np.ascontiguousarray(bits, dtype=np.uint64)
+    assert b.size >= (m + 63) // 64
+    if k is None:
+        pc = int(np.unpackbits(b.view(np.uint8), bitorder="little")[:m].sum())
+        k = rice_param(m, pc)
+    cap = 64
+    while True:
+        out = np.zeros(cap, dtype=np.uint8)
+        cnt = _u64(0)
+        nb = int(lib().oracle_rice_encode(_ptr(b), m, k, _ptr(out), cap, ctypes.byref(cnt)))
+        if nb != (1 << 64) - 1:
+            return out[:(nb + 7) // 8].copy(), nb, int(cnt.value), k
+        cap *= 4
+
+
+def rice_decode(stream: np.ndarray, nbits: int, k: int, count: int, m: int) -> np.ndarray:
+    s = np.ascontiguousarray(stream, dtype=np.uint8)
+    if s.size == 0:
+        s = np.zeros(1, dtype=np.uint8)
+    out = np.zeros((m + 63) // 64, dtype=np.uint64)
+    rc = lib().oracle_rice_decode(_ptr(s), nbits, k, count, m, _ptr(out))
+    if rc != OK:
+        raise ValueError("rice stream does not decode")
     return out
 
 

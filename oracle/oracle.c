@@ -13,6 +13,8 @@
  *   oracle_cuckoo_insert  Section 5.3 (blocked cuckoo insertion, FIFO collection)
  *   oracle_bloom_*        Section 7 (interest vectors, global interest vector,
  *                         window of deltas)
+ *   oracle_rice_*         Section 7, GetUpdates: compressed deltas (Rice code
+ *                         of the gaps between set bits, taken as the encoding)
  */
 #include "oracle.h"
 
@@ -428,4 +430,74 @@ int oracle_bloom_contains(const oracle_bloom *b, const uint64_t *positions) {
         if (!set) return 0;
     }
     return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compressed deltas: Golomb-Rice code of the gaps between set bits          */
+/* ------------------------------------------------------------------------ */
+
+uint32_t oracle_rice_param(uint64_t m, uint64_t count) {
+    if (count == 0) return 0;
+    uint64_t g = (m - count) / count;
+    uint32_t k = 0;
+    while (g >= 2) {   /* floor(log2 g) for g >= 1 */
+        g >>= 1;
+        k++;
+    }
+    return k;
+}
+
+static int put_bit(uint8_t *out, uint64_t cap, uint64_t pos, int bit) {
+    if (pos / 8 >= cap) return 0;
+    if (bit) out[pos / 8] |= (uint8_t)(1u << (pos % 8));
+    return 1;
+}
+
+uint64_t oracle_rice_encode(const uint64_t *bits, uint64_t m, uint32_t k, uint8_t *out,
+                            uint64_t cap, uint64_t *count) {
+    uint64_t pos = 0, n = 0;
+    int64_t prev = -1;
+    for (uint64_t j = 0; j < cap; j++) out[j] = 0;
+    for (uint64_t p = 0; p < m; p++) {
+        if (!((bits[p / 64] >> (p % 64)) & 1u)) continue;
+        uint64_t gap = (uint64_t)((int64_t)p - prev - 1);
+        uint64_t q = gap >> k;
+        for (uint64_t i = 0; i < q; i++)
+            if (!put_bit(out, cap, pos++, 1)) return UINT64_MAX;
+        if (!put_bit(out, cap, pos++, 0)) return UINT64_MAX;
+        for (uint32_t i = 0; i < k; i++)
+            if (!put_bit(out, cap, pos++, (int)((gap >> i) & 1u))) return UINT64_MAX;
+        prev = (int64_t)p;
+        n++;
+    }
+    if (count) *count = n;
+    return pos;
+}
+
+int oracle_rice_decode(const uint8_t *in, uint64_t nbits, uint32_t k, uint64_t count, uint64_t m,
+                       uint64_t *bits) {
+    uint64_t words = (m + 63) / 64, pos = 0;
+    int64_t prev = -1;
+    for (uint64_t w = 0; w < words; w++) bits[w] = 0;
+    for (uint64_t c = 0; c < count; c++) {
+        uint64_t q = 0;
+        for (;;) {
+            if (pos >= nbits) return ORACLE_EINVAL;
+            int b = (in[pos / 8] >> (pos % 8)) & 1;
+            pos++;
+            if (!b) break;
+            q++;
+        }
+        uint64_t r = 0;
+        for (uint32_t i = 0; i < k; i++) {
+            if (pos >= nbits) return ORACLE_EINVAL;
+            r |= (uint64_t)((in[pos / 8] >> (pos % 8)) & 1) << i;
+            pos++;
+        }
+        uint64_t p = (uint64_t)(prev + 1) + (q << k) + r;
+        if (p >= m) return ORACLE_EINVAL;
+        bits[p / 64] |= 1ull << (p % 64);
+        prev = (int64_t)p;
+    }
+    return ORACLE_OK;
 }

@@ -106,6 +106,31 @@ void oracle_bloom_get(const oracle_bloom *b, uint64_t *out_words);
 /* 1 if all k positions are set in the global interest vector. */
 int oracle_bloom_contains(const oracle_bloom *b, const uint64_t *positions);
 
+/* ---- Compressed interest-vector deltas (Section 7, GetUpdates) ---------
+ * The paper sends Bloom-filter deltas compressed; the encoding taken here is
+ * the Golomb-Rice code of the gaps between consecutive set bits: for set
+ * bits p_0 < p_1 < ..., gap_i = p_i - p_{i-1} - 1 (p_{-1} = -1), written as
+ * q = gap_i >> k one-bits, a zero bit, then the k low bits of gap_i (least
+ * significant first).  The stream is packed LSB-first: stream bit j is bit
+ * (j % 8) of byte j / 8. */
+
+/* Rice parameter for `count` set bits among m: 0 if count = 0 or the mean
+ * gap g = (m - count) / count (integer division) is 0, else floor(log2 g). */
+uint32_t oracle_rice_param(uint64_t m, uint64_t count);
+
+/* Encodes the set bits of an m-bit vector (ceil(m/64) words; bits >= m
+ * ignored) with parameter k.  Writes ceil(nbits/8) bytes to out (cap bytes
+ * available) and returns nbits, or UINT64_MAX if the stream would not fit;
+ * *count = set bits encoded. */
+uint64_t oracle_rice_encode(const uint64_t *bits, uint64_t m, uint32_t k, uint8_t *out,
+                            uint64_t cap, uint64_t *count);
+
+/* Decodes `count` codes of parameter k from a stream of nbits bits into an
+ * m-bit vector (ceil(m/64) words, cleared first).  Returns ORACLE_OK, or
+ * ORACLE_EINVAL if the stream is short or a position falls at or past m. */
+int oracle_rice_decode(const uint8_t *in, uint64_t nbits, uint32_t k, uint64_t count, uint64_t m,
+                       uint64_t *bits);
+
 #ifdef __cplusplus
 }
 #endif
