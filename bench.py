@@ -197,12 +197,13 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--legs", default="head,head_m4rm,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large",
+    ap.add_argument("--legs", default="head,head_m4rm,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large,getupdates",
                     help="comma list of: head (B=256, timed headline: the automatic choice, the "
                          "tensor-core kernel), head_m4rm / head_lop3 (B=256 on the Four-Russians / "
                          "register-tiled LOP3 kernel), plain (B=1), b32, masked (serialized-PIR "
                          "masked replies at B=256 and B=1), sharded (the table in 4 row shards "
-                         "on this GPU, partial replies XOR-combined), "
+                         "on this GPU, partial replies XOR-combined), getupdates (compressed "
+                         "interest-vector deltas), "
                          "e2e (host buffers), serve, cpu (oracle baseline), multi (64 uneven "
                          "tables, one graph-captured launch), large (4 GiB table, B=1024); "
                          "serve_sweep (not default: tables filling a 64 GiB budget, Poisson "
@@ -449,6 +450,8 @@ def main() -> None:
         cpu = {"value": sample / cdt, "unit": "reads/s", "cores": 1, "kind": "oracle",
                "sample": f"{sample} reads of the 128 MiB table (single-threaded C)"}
 
+    getupdates = getupdates_leg(talekpir, synth, torch, stream) if ("getupdates" in args.legs and rank == 0) else None
+
     sweep = None
     if "serve_sweep" in args.legs and rank == 0:
         sweep = serve_sweep_leg(talekpir, synth, torch, stream, args)
@@ -484,6 +487,7 @@ def main() -> None:
             "serve": serve,
             "multi_table": multi,
             "serve_sweep": sweep,
+            "getupdates": getupdates,
             "large_table": large,
             "cpu_baseline": cpu,
         }
@@ -495,6 +499,39 @@ def main() -> None:
 
 
 SHARDS = 4
+
+
+def getupdates_leg(talekpir, synth, torch, stream) -> dict:
+    """Compressed GetUpdates: a window of 8 Bloom deltas over m = 2^24 bits,
+    131 072 writes x 4 positions per delta (1 M writes in the window), each
+    delta and the global interest vector Rice-coded on the device."""
+    m, kpos, window, per = 1 << 24, 4, 8, 1 << 17
+    db = talekpir.DB(64, 4, 64)
+    db.bloom_create(m, kpos, window, per)
+    keys = synth.write_keys(window * per, seed=13)
+    pos = synth.bloom_positions(keys, m, kpos)
+    for i in range(0, len(pos), 1 << 16):
+        assert db.bloom_insert_batch(pos[i:i + (1 << 16)]) == talekpir.OK
+    out = {"m_bits": m, "k": kpos, "window": window, "writes_per_delta": per,
+           "raw_bytes": m // 8}
+    _, nb, cnt, k = db.bloom_get_compressed(1)
+    out.update({"delta_bits_set": cnt, "delta_compressed_bytes": (nb + 7) // 8, "delta_rice_k": k})
+    _, nb, cnt, k = db.bloom_get_compressed(0)
+    out.update({"global_bits_set": cnt, "global_compressed_bytes": (nb + 7) // 8, "global_rice_k": k})
+    # device time of one delta's encoding (a delta is encoded once and served
+    # to every client that asks)
+    vec = torch.zeros(m // 64, dtype=torch.int64, device="cuda")
+    vec.copy_(torch.from_numpy(db.bloom_get().view(np.int64)))
+    cap = m // 4
+    dout = torch.empty(cap // 4, dtype=torch.int32, device="cuda")
+    res = torch.empty(3, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        talekpir.rice_encode_async(vec, m, dout, cap, res, -1, stream.cuda_stream)
+    ms = _events_ms(torch, stream, lambda: talekpir.rice_encode_async(vec, m, dout, cap, res, -1,
+                                                                       stream.cuda_stream), 10)
+    out["global_encode_us"] = ms * 1000
+    db.close()
+    return out
 
 
 def sharded_leg(talekpir, torch, stream, T, dR, args, legs) -> dict:

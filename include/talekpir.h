@@ -283,6 +283,28 @@ tpir_status tpir_bloom_or_vector(tpir_db *db, const uint64_t *vec);
 /* GetUpdates: the global interest vector, ceil(m/64) words (host). */
 tpir_status tpir_bloom_get(tpir_db *db, uint64_t *out_words);
 
+/* Compressed GetUpdates (Section 7: the servers send compressed Bloom-filter
+ * deltas; the paper fixes no encoding).  The encoding is the Golomb-Rice code
+ * of the gaps between set bits: for set bits p_0 < p_1 < ... and p_{-1} = -1,
+ * gap_i = p_i - p_{i-1} - 1 is written as (gap_i >> k) one-bits, a zero bit,
+ * then the k low bits of gap_i, least significant first; the stream is
+ * packed LSB-first (stream bit j = bit j % 8 of byte j / 8).  k < 0 chooses
+ * k = floor(log2 g) for the mean gap g = (m - count) / count (0 if g = 0 or
+ * count = 0).  The decoder needs m, k and count.
+ * tpir_bloom_get_compressed encodes, on the device, which = 0: the global
+ * interest vector, or which = i >= 1: the i-th most recent delta of the window
+ * (1 = the current one); writes ceil(nbits/8) bytes to the host buffer out.
+ * Returns TPIR_ENOMEM (with *nbits = UINT64_MAX or the stream length) if the
+ * stream does not fit cap_bytes; EINVAL for which > window. */
+tpir_status tpir_bloom_get_compressed(tpir_db *db, uint32_t which, int32_t k, void *out,
+                                      uint64_t cap_bytes, uint64_t *nbits, uint64_t *count,
+                                      uint32_t *k_used);
+/* The same encoding of any m-bit vector in device memory, on `stream`:
+ * d_result (device, 3 words) receives nbits (UINT64_MAX if the stream would
+ * pass cap_bytes, a multiple of 4), count and k; d_out 4-byte aligned. */
+tpir_status tpir_rice_encode_async(const uint64_t *d_bits, uint64_t m, int32_t k, void *d_out,
+                                   uint64_t cap_bytes, uint64_t *d_result, void *stream);
+
 /* ---- serving: continuous batching over resident tables -------------------
  * A server thread admits reads and writes as they arrive, keeps tables
  * resident under an HBM budget, applies each table's writes in arrival order,

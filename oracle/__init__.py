@@ -87,6 +87,8 @@ def lib():
         L.oracle_bloom_or_vector.restype = None
         L.oracle_bloom_get.argtypes = [_vp, _vp]
         L.oracle_bloom_get.restype = None
+        L.oracle_bloom_delta.argtypes = [_vp, _u32, _vp]
+        L.oracle_bloom_delta.restype = ctypes.c_int
         L.oracle_bloom_contains.argtypes = [_vp, _vp]
         L.oracle_bloom_contains.restype = ctypes.c_int
         _lib = L
@@ -259,6 +261,13 @@ class Bloom:
     def get(self) -> np.ndarray:
         out = np.empty((self.m + 63) // 64, dtype=np.uint64)
         lib().oracle_bloom_get(self.h, _ptr(out))
+        return out
+
+    def delta(self, age: int) -> np.ndarray:
+        """The age-th most recent delta (1 = current)."""
+        out = np.empty((self.m + 63) // 64, dtype=np.uint64)
+        if lib().oracle_bloom_delta(self.h, age, _ptr(out)) != OK:
+            raise ValueError("no such delta")
         return out
 
     def contains(self, positions) -> bool:

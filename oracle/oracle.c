@@ -421,6 +421,16 @@ void oracle_bloom_get(const oracle_bloom *b, uint64_t *out_words) {
             if (b->bits[(uint64_t)j * b->m + p]) out_words[p >> 6] |= 1ULL << (p & 63);
 }
 
+int oracle_bloom_delta(const oracle_bloom *b, uint32_t age, uint64_t *out_words) {
+    if (age == 0 || age > b->window) return ORACLE_EINVAL;
+    uint32_t j = (b->cur + b->window - (age - 1)) % b->window;
+    uint64_t words = (b->m + 63) / 64;
+    for (uint64_t w = 0; w < words; w++) out_words[w] = 0;
+    for (uint64_t p = 0; p < b->m; p++)
+        if (b->bits[(uint64_t)j * b->m + p]) out_words[p >> 6] |= 1ULL << (p & 63);
+    return ORACLE_OK;
+}
+
 int oracle_bloom_contains(const oracle_bloom *b, const uint64_t *positions) {
     for (uint32_t i = 0; i < b->k; i++) {
         if (positions[i] >= b->m) return 0;

@@ -103,6 +103,9 @@ int oracle_bloom_insert(oracle_bloom *b, const uint64_t *positions);
 void oracle_bloom_or_vector(oracle_bloom *b, const uint64_t *vec);
 /* Global interest vector = OR of the deltas in the window (ceil(m/64) words). */
 void oracle_bloom_get(const oracle_bloom *b, uint64_t *out_words);
+/* The age-th most recent delta (age 1 = the current one, up to window), as
+ * ceil(m/64) words; returns ORACLE_EINVAL for an age outside 1..window. */
+int oracle_bloom_delta(const oracle_bloom *b, uint32_t age, uint64_t *out_words);
 /* 1 if all k positions are set in the global interest vector. */
 int oracle_bloom_contains(const oracle_bloom *b, const uint64_t *positions);
 

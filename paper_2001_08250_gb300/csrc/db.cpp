@@ -487,6 +487,8 @@ void tpir_db_destroy(tpir_db* db) {
   cudaFree(db->d_out);
   cudaFree(db->bloom.d_deltas);
   cudaFree(db->bloom.d_out);
+  cudaFree(db->bloom.d_rice);
+  cudaFree(db->bloom.d_rice_res);
   if (db->last_write) cudaEventDestroy(db->last_write);
   if (db->stream_mark) cudaEventDestroy(db->stream_mark);
   if (db->stream) cudaStreamDestroy(db->stream);
@@ -794,6 +796,47 @@ tpir_status tpir_bloom_or_vector(tpir_db* db, const uint64_t* vec) {
   if (e != cudaSuccess) return cuda_status(e);
   bl.count += 1;
   return TPIR_OK;
+}
+
+tpir_status tpir_bloom_get_compressed(tpir_db* db, uint32_t which, int32_t k, void* out,
+                                      uint64_t cap_bytes, uint64_t* nbits, uint64_t* count,
+                                      uint32_t* k_used) {
+  if (nbits) *nbits = 0;
+  if (!db || !out || !db->bloom.d_deltas || which > db->bloom.window || k > 63) return TPIR_EINVAL;
+  tpir_bloom_state& bl = db->bloom;
+  const uint64_t cap = (cap_bytes + 3) / 4 * 4;
+  if (!grow_dev(reinterpret_cast<void**>(&bl.d_rice), &bl.rice_cap, cap)) return TPIR_ENOMEM;
+  if (!bl.d_rice_res && cudaMalloc(reinterpret_cast<void**>(&bl.d_rice_res), 3 * 8) != cudaSuccess)
+    return TPIR_ENOMEM;
+  // 0: the global interest vector; i >= 1: the i-th most recent delta
+  const uint64_t* vec = bl.d_out;
+  cudaError_t e = cudaSuccess;
+  if (which == 0)
+    e = launch_bloom_union(bl.d_deltas, bl.window, bl.words, bl.d_out, db->stream);
+  else
+    vec = bl.d_deltas + static_cast<uint64_t>((bl.cur + bl.window - (which - 1)) % bl.window) * bl.words;
+  const RiceRequest rq{vec, bl.m, k, bl.d_rice, cap / 4, bl.d_rice_res};
+  if (e == cudaSuccess) e = launch_rice_encode(&rq, 1, db->stream);
+  uint64_t res[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res, bl.d_rice_res, sizeof(res), cudaMemcpyDeviceToHost, db->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (count) *count = res[1];
+  if (k_used) *k_used = static_cast<uint32_t>(res[2]);
+  if (nbits) *nbits = res[0];
+  if (res[0] == ~0ull || (res[0] + 7) / 8 > cap_bytes) return TPIR_ENOMEM;  // stream past cap
+  if (res[0]) e = cudaMemcpy(out, bl.d_rice, (res[0] + 7) / 8, cudaMemcpyDeviceToHost);
+  return cuda_status(e);
+}
+
+tpir_status tpir_rice_encode_async(const uint64_t* d_bits, uint64_t m, int32_t k, void* d_out,
+                                   uint64_t cap_bytes, uint64_t* d_result, void* stream) {
+  if (!d_bits || !d_out || !d_result || m == 0 || k > 63 || (cap_bytes & 3) ||
+      (reinterpret_cast<uintptr_t>(d_out) & 3) || (reinterpret_cast<uintptr_t>(d_bits) & 7) ||
+      (reinterpret_cast<uintptr_t>(d_result) & 7))
+    return TPIR_EINVAL;
+  const RiceRequest rq{d_bits, m, k, static_cast<uint32_t*>(d_out), cap_bytes / 4, d_result};
+  return cuda_status(launch_rice_encode(&rq, 1, static_cast<cudaStream_t>(stream)));
 }
 
 tpir_status tpir_bloom_get(tpir_db* db, uint64_t* out_words) {

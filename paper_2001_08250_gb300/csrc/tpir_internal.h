@@ -177,6 +177,17 @@ cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, 
 constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel beats LOP3
 constexpr uint32_t kTensorMinB = 96;  // batch from which the tensor-core kernel beats LOP3
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
+// Rice coding of sparse bit vectors (rice.cu): one CTA per vector.
+constexpr uint32_t kRiceMaxJobs = 64;
+struct RiceRequest {
+  const uint64_t* bits;  // ceil(m/64) words
+  uint64_t m;
+  int32_t k;             // < 0: chosen from the set-bit count
+  uint32_t* out;         // cap_words 32-bit words
+  uint64_t cap_words;
+  uint64_t* result;      // device: nbits (UINT64_MAX if past cap), count, k
+};
+cudaError_t launch_rice_encode(const RiceRequest* reqs, uint32_t count, cudaStream_t st);
 
 // Host cuckoo metadata (cuckoo.cpp): same placement rules as the paper's
 // Section 5.3 insertion; emits the device moves of one insertion.
@@ -233,6 +244,9 @@ struct tpir_bloom_state {
   uint32_t cur = 0, count = 0;
   uint64_t* d_deltas = nullptr;   // window x words
   uint64_t* d_out = nullptr;      // words
+  uint32_t* d_rice = nullptr;     // compressed-stream staging (GetUpdates)
+  uint64_t rice_cap = 0;          // its bytes
+  uint64_t* d_rice_res = nullptr; // nbits, count, k
 };
 
 struct tpir_db {

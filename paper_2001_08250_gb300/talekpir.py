@@ -72,6 +72,8 @@ _SIGS = [
     ("tpir_db_create", _vp, [_u64, _u32, _u32]),
     ("tpir_db_destroy", None, [_vp]),
     ("tpir_db_create_shard", _vp, [_u64, _u64, _u64, _u32, _u32]),
+    ("tpir_bloom_get_compressed", ctypes.c_int, [_vp, _u32, ctypes.c_int32, _vp, _u64, _vp, _vp, _vp]),
+    ("tpir_rice_encode_async", ctypes.c_int, [_vp, _u64, ctypes.c_int32, _vp, _u64, _vp, _vp]),
     ("tpir_db_shard_info", ctypes.c_int, [_vp, _vp, _vp]),
     ("tpir_shard_plan", ctypes.c_int, [_u64, _u32, _u32, _vp, _vp]),
     ("tpir_db_info", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
@@ -330,6 +332,17 @@ class DB:
         v = np.ascontiguousarray(vec, dtype=np.uint64)
         _check(lib().tpir_bloom_or_vector(self.h, _hptr(v)), "tpir_bloom_or_vector")
 
+    def bloom_get_compressed(self, which: int = 0, k: int = -1, cap: int | None = None):
+        """Compressed GetUpdates: (stream bytes, nbits, count, k) of the global
+        interest vector (which = 0) or of the which-th most recent delta."""
+        cap = cap or ((self.bloom_m + 63) // 64) * 8 * 2 + 64
+        out = np.zeros(cap, dtype=np.uint8)
+        nb, cnt, ku = _u64(), _u64(), _u32()
+        _check(lib().tpir_bloom_get_compressed(self.h, int(which), int(k), _hptr(out), cap,
+                                               ctypes.byref(nb), ctypes.byref(cnt), ctypes.byref(ku)),
+               "tpir_bloom_get_compressed")
+        return out[:(nb.value + 7) // 8].copy(), nb.value, cnt.value, ku.value
+
     def bloom_get(self) -> np.ndarray:
         out = np.empty((self.bloom_m + 63) // 64, dtype=np.uint64)
         _check(lib().tpir_bloom_get(self.h, _hptr(out)), "tpir_bloom_get")
@@ -346,6 +359,14 @@ def tune_load(path: str) -> None:
 
 def tune_clear() -> None:
     _check(lib().tpir_tune_clear(), "tpir_tune_clear")
+
+
+def rice_encode_async(d_bits, m: int, d_out, cap_bytes: int, d_result, k: int = -1,
+                      stream=None) -> None:
+    """Rice code of an m-bit device vector into d_out; d_result (3 x uint64
+    on the device) receives nbits, count and k."""
+    _check(lib().tpir_rice_encode_async(_dptr(d_bits), int(m), int(k), _dptr(d_out), int(cap_bytes),
+                                        _dptr(d_result), _stream(stream)), "tpir_rice_encode_async")
 
 
 def shard_plan(n_total: int, parts: int) -> list[tuple[int, int]]:

@@ -236,3 +236,54 @@ def test_bounded_wait_gives_up_and_context_survives():
         db.load(T)
         assert np.array_equal(db.read_batch(R), oracle.read_batch(T, n, d, z, R))
     assert talekpir.lib().tpir_selftest_wait_timeout(0) == talekpir.EINVAL
+
+
+def test_real_read_with_second_bucket_retry():
+    """A client's RealRead (Section 5.4): messages written through the cuckoo
+    path sit in one of their two buckets (evictions may move them), so a read
+    asks for the first bucket with three XOR shares (Section 2), looks for the
+    message's tag among the d slots of the reconstructed bucket, and only if
+    it is absent asks for the second bucket.  Every message is found, some
+    only on the retry; each reconstructed bucket equals the oracle table's."""
+    require_cuda()
+    n, d, z, count = 256, 4, 64, 700
+    keys = synth.write_keys(count, seed=41)
+    b1, b2 = synth.bucket_pairs(keys, n)
+    msgs = synth.messages(count, z, seed=41)
+    msgs[:, :8] = np.arange(1, count + 1, dtype=np.uint64).view(np.uint8).reshape(count, 8)  # tag
+    db = talekpir.DB(n, d, z)
+    db.set_policy(0, 500, 41)
+    oc = oracle.Cuckoo(n, d, z, 0, 500, seed=41)
+    live = []
+    for i in range(count):
+        rc, _ = db.write(int(b1[i]), int(b2[i]), msgs[i])
+        assert rc == oc.insert(int(b1[i]), int(b2[i]), msgs[i])[0]
+        if rc == talekpir.OK:
+            live.append(i)
+    T = oc.table()
+    want = np.array(live[::7])
+    retries = 0
+
+    def read_bucket(targets):
+        sh = synth.xor_shares(n, targets, 3, seed=42 + len(targets))
+        got = db.read_batch(sh.reshape(len(targets) * 3, -1)).reshape(len(targets), 3, -1)
+        return got[:, 0] ^ got[:, 1] ^ got[:, 2]
+
+    first = read_bucket(b1[want].astype(np.int64))
+    assert np.array_equal(first, T[b1[want]])
+    missing = []
+    for j, i in enumerate(want):
+        slots = first[j].reshape(d, z)
+        if not any(np.array_equal(s, msgs[i]) for s in slots):
+            missing.append(i)
+    retries = len(missing)
+    if missing:
+        second = read_bucket(b2[np.array(missing)].astype(np.int64))
+        assert np.array_equal(second, T[b2[np.array(missing)]])
+        for j, i in enumerate(missing):
+            slots = second[j].reshape(d, z)
+            assert any(np.array_equal(s, msgs[i]) for s in slots), i
+    assert retries > 0                      # some messages live in their second bucket
+    assert retries < len(want)
+    db.close()
+    assert talekpir.device_status() == talekpir.OK

@@ -76,3 +76,29 @@ def test_invalid_position_rejected():
     b = oracle.Bloom(100, 2)
     assert b.insert([5, 100]) == oracle.EINVAL
     assert not b.get().any()
+
+
+def test_delta_accessor_partitions_the_window():
+    """The deltas of the window OR to the global interest vector, the current
+    delta holds exactly the latest writes, and ages outside the window fail."""
+    import pytest
+    from paper_2001_08250_gb300 import synth
+    m, k, window, per = 4096, 3, 4, 5
+    b = oracle.Bloom(m, k, window, per)
+    keys = synth.write_keys(13, seed=31)
+    pos = synth.bloom_positions(keys, m, k)
+    for p in pos:
+        assert b.insert(p) == 0
+    acc = np.zeros((m + 63) // 64, dtype=np.uint64)
+    for age in range(1, window + 1):
+        acc |= b.delta(age)
+    assert np.array_equal(acc, b.get())
+    # 13 writes, 5 per delta: the current delta holds writes 10..12
+    cur = b.delta(1)
+    exp = np.zeros_like(cur)
+    for p in pos[10:]:
+        for q in p:
+            exp[int(q) // 64] |= np.uint64(1) << np.uint64(int(q) % 64)
+    assert np.array_equal(cur, exp)
+    with pytest.raises(ValueError):
+        b.delta(window + 1)
