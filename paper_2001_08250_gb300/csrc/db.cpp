@@ -489,6 +489,7 @@ void tpir_db_destroy(tpir_db* db) {
   cudaFree(db->bloom.d_out);
   cudaFree(db->bloom.d_rice);
   cudaFree(db->bloom.d_rice_res);
+  cudaFree(db->bloom.d_rice_scratch);
   if (db->last_write) cudaEventDestroy(db->last_write);
   if (db->stream_mark) cudaEventDestroy(db->stream_mark);
   if (db->stream) cudaStreamDestroy(db->stream);
@@ -816,7 +817,10 @@ tpir_status tpir_bloom_get_compressed(tpir_db* db, uint32_t which, int32_t k, vo
   else
     vec = bl.d_deltas + static_cast<uint64_t>((bl.cur + bl.window - (which - 1)) % bl.window) * bl.words;
   const RiceRequest rq{vec, bl.m, k, bl.d_rice, cap / 4, bl.d_rice_res};
-  if (e == cudaSuccess) e = launch_rice_encode(&rq, 1, db->stream);
+  if (!grow_dev(reinterpret_cast<void**>(&bl.d_rice_scratch), &bl.rice_scratch_cap,
+                rice_scratch_bytes(bl.m)))
+    return TPIR_ENOMEM;
+  if (e == cudaSuccess) e = launch_rice_encode(rq, bl.d_rice_scratch, db->stream);
   uint64_t res[3] = {0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(res, bl.d_rice_res, sizeof(res), cudaMemcpyDeviceToHost, db->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
@@ -836,7 +840,16 @@ tpir_status tpir_rice_encode_async(const uint64_t* d_bits, uint64_t m, int32_t k
       (reinterpret_cast<uintptr_t>(d_result) & 7))
     return TPIR_EINVAL;
   const RiceRequest rq{d_bits, m, k, static_cast<uint32_t*>(d_out), cap_bytes / 4, d_result};
-  return cuda_status(launch_rice_encode(&rq, 1, static_cast<cudaStream_t>(stream)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // scratch from the stream-ordered allocator: calls on other streams do not share it
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, rice_scratch_bytes(m), st);
+  if (e == cudaSuccess) e = launch_rice_encode(rq, scratch, st);
+  if (scratch) {
+    const cudaError_t f = cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = f;
+  }
+  return cuda_status(e);
 }
 
 tpir_status tpir_bloom_get(tpir_db* db, uint64_t* out_words) {

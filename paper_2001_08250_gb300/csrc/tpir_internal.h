@@ -177,8 +177,7 @@ cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, 
 constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel beats LOP3
 constexpr uint32_t kTensorMinB = 96;  // batch from which the tensor-core kernel beats LOP3
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
-// Rice coding of sparse bit vectors (rice.cu): one CTA per vector.
-constexpr uint32_t kRiceMaxJobs = 64;
+// Rice coding of sparse bit vectors (rice.cu).
 struct RiceRequest {
   const uint64_t* bits;  // ceil(m/64) words
   uint64_t m;
@@ -187,7 +186,10 @@ struct RiceRequest {
   uint64_t cap_words;
   uint64_t* result;      // device: nbits (UINT64_MAX if past cap), count, k
 };
-cudaError_t launch_rice_encode(const RiceRequest* reqs, uint32_t count, cudaStream_t st);
+// scratch: rice_scratch_bytes(m) of device memory, free until the stream
+// passes the encode
+size_t rice_scratch_bytes(uint64_t m);
+cudaError_t launch_rice_encode(const RiceRequest& q, void* scratch, cudaStream_t st);
 
 // Host cuckoo metadata (cuckoo.cpp): same placement rules as the paper's
 // Section 5.3 insertion; emits the device moves of one insertion.
@@ -247,6 +249,8 @@ struct tpir_bloom_state {
   uint32_t* d_rice = nullptr;     // compressed-stream staging (GetUpdates)
   uint64_t rice_cap = 0;          // its bytes
   uint64_t* d_rice_res = nullptr; // nbits, count, k
+  void* d_rice_scratch = nullptr;  // per-block scan values
+  uint64_t rice_scratch_cap = 0;
 };
 
 struct tpir_db {
