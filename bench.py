@@ -415,10 +415,13 @@ def main() -> None:
     hO = torch.empty((USERS, row), dtype=torch.uint8).pin_memory().numpy()
 
     def e2e_step():
-        for i, b0 in enumerate(range(0, USERS, B_HEAD)):
-            nb = min(B_HEAD, USERS - b0)
-            rc = L.tpir_read_batch(dbs[i % COPIES].h, hR[b0:b0 + nb].ctypes.data, nb,
-                                   hO[b0:b0 + nb].ctypes.data)
+        # each table copy serves a quarter of the step's reads through the
+        # pipelined host-buffer call (batches of B_HEAD; copies overlap scans)
+        q = (USERS + COPIES - 1) // COPIES
+        for c in range(COPIES):
+            b0, nb = c * q, min(q, USERS - c * q)
+            rc = L.tpir_read_batch_pipelined(dbs[c].h, hR[b0:b0 + nb].ctypes.data, nb, B_HEAD,
+                                             hO[b0:b0 + nb].ctypes.data)
             assert rc == 0, rc
     e2e = None
     if "e2e" in args.legs:

@@ -158,6 +158,15 @@ tpir_status tpir_write_noalloc(tpir_db *db, uint64_t b1, uint64_t b2, const void
  * B = 0 is a no-op.  Sees every write made before the call. */
 tpir_status tpir_read_batch(tpir_db *db, const uint64_t *req_bits, uint32_t B, void *out);
 
+/* Synchronous, for request sets larger than one batch: B_total rows of
+ * req_bits (host) in batches of `batch`, replies into out (host, B_total x
+ * row_bytes).  Three device slots rotate: each batch's rows are copied in two
+ * batches ahead of its scan and its replies copied out after it, on a copy
+ * stream, so the copies overlap the scans (with pinned host buffers; pageable
+ * ones work but serialise).  Same replies as tpir_read_batch on each batch. */
+tpir_status tpir_read_batch_pipelined(tpir_db *db, const uint64_t *req_bits, uint64_t B_total,
+                                      uint32_t batch, void *out);
+
 /* Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream):
  * d_req_bits and d_out are device buffers that must stay valid until the
  * stream reaches this point.  d_out must not overlap d_req_bits or the table.

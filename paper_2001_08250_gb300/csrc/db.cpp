@@ -490,6 +490,11 @@ void tpir_db_destroy(tpir_db* db) {
   cudaFree(db->bloom.d_rice);
   cudaFree(db->bloom.d_rice_res);
   cudaFree(db->bloom.d_rice_scratch);
+  if (db->copy_stream) cudaStreamSynchronize(db->copy_stream);
+  cudaFree(db->d_pipe);
+  for (cudaEvent_t ev : db->pipe_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (db->copy_stream) cudaStreamDestroy(db->copy_stream);
   if (db->last_write) cudaEventDestroy(db->last_write);
   if (db->stream_mark) cudaEventDestroy(db->stream_mark);
   if (db->stream) cudaStreamDestroy(db->stream);
@@ -605,6 +610,68 @@ static tpir_status read_batch_sync(tpir_db* db, const uint64_t* req_bits, uint32
   if (s != TPIR_OK) return s;
   e = cudaMemcpyAsync(out, db->d_out, ob, cudaMemcpyDeviceToHost, db->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = 0;
+  if (read_device_status_and_clear(&st) != 0) return TPIR_ECUDA;
+  return st ? static_cast<tpir_status>(st) : TPIR_OK;
+}
+
+tpir_status tpir_read_batch_pipelined(tpir_db* db, const uint64_t* req_bits, uint64_t B_total,
+                                      uint32_t batch, void* out) {
+  if (!db) return TPIR_EINVAL;
+  if (B_total == 0) return TPIR_OK;
+  if (!req_bits || !out || batch == 0) return TPIR_EINVAL;
+  constexpr int kSlots = 3;
+  const uint64_t rb = static_cast<uint64_t>(batch) * db->words64 * 8;
+  const uint64_t ob = static_cast<uint64_t>(batch) * db->row_bytes;
+  const uint64_t ra = (rb + 255) / 256 * 256, oa = (ob + 255) / 256 * 256;
+  if (!grow_dev(reinterpret_cast<void**>(&db->d_pipe), &db->pipe_cap, kSlots * (ra + oa)))
+    return TPIR_ENOMEM;
+  cudaError_t e = cudaSuccess;
+  if (!db->copy_stream) e = cudaStreamCreateWithFlags(&db->copy_stream, cudaStreamNonBlocking);
+  for (int i = 0; e == cudaSuccess && i < 3 * kSlots; ++i)
+    if (!db->pipe_ev[i]) e = cudaEventCreateWithFlags(&db->pipe_ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaStream_t cp = db->copy_stream, cs = db->stream;
+  cudaEvent_t* in_done = db->pipe_ev;              // request rows copied in
+  cudaEvent_t* scan_done = db->pipe_ev + kSlots;   // scan of the slot done
+  cudaEvent_t* out_done = db->pipe_ev + 2 * kSlots;  // replies copied out
+  const uint64_t nbatch = (B_total + batch - 1) / batch;
+  auto req_of = [&](uint64_t i) { return reinterpret_cast<uint64_t*>(db->d_pipe + (i % kSlots) * (ra + oa)); };
+  auto out_of = [&](uint64_t i) { return db->d_pipe + (i % kSlots) * (ra + oa) + ra; };
+  auto rows = [&](uint64_t i) { return static_cast<uint32_t>(std::min<uint64_t>(batch, B_total - i * batch)); };
+  // copy-in of batch i: into its slot, once the scan that last read the slot is done
+  auto copy_in = [&](uint64_t i) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    if (i >= kSlots) r = cudaStreamWaitEvent(cp, scan_done[i % kSlots], 0);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(req_of(i), req_bits + i * batch * db->words64,
+                          static_cast<uint64_t>(rows(i)) * db->words64 * 8, cudaMemcpyHostToDevice, cp);
+    if (r == cudaSuccess) r = cudaEventRecord(in_done[i % kSlots], cp);
+    return r;
+  };
+  // copy-in runs two batches ahead, so it overlaps the scans; copy-out follows each scan
+  for (uint64_t i = 0; e == cudaSuccess && i < std::min<uint64_t>(2, nbatch); ++i) e = copy_in(i);
+  for (uint64_t i = 0; e == cudaSuccess && i < nbatch; ++i) {
+    const int s = static_cast<int>(i % kSlots);
+    e = cudaStreamWaitEvent(cs, in_done[s], 0);
+    if (e == cudaSuccess && i >= kSlots) e = cudaStreamWaitEvent(cs, out_done[s], 0);
+    if (e != cudaSuccess) break;
+    const tpir_status st = enqueue_read(db, req_of(i), rows(i), out_of(i), cs);
+    if (st != TPIR_OK) {
+      cudaStreamSynchronize(cp);
+      return st;
+    }
+    e = cudaEventRecord(scan_done[s], cs);
+    if (e == cudaSuccess && i + 2 < nbatch) e = copy_in(i + 2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cp, scan_done[s], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + i * batch * db->row_bytes, out_of(i),
+                          static_cast<uint64_t>(rows(i)) * db->row_bytes, cudaMemcpyDeviceToHost, cp);
+    if (e == cudaSuccess) e = cudaEventRecord(out_done[s], cp);
+  }
+  const cudaError_t e2 = cudaStreamSynchronize(cp);
+  if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return cuda_status(e);
   int st = 0;
   if (read_device_status_and_clear(&st) != 0) return TPIR_ECUDA;

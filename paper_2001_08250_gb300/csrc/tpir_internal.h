@@ -278,6 +278,12 @@ struct tpir_db {
   uint64_t* d_req = nullptr;
   uint8_t* d_out = nullptr;
   uint64_t req_cap = 0, out_cap = 0;
+  // pipelined host-buffer reads: a copy stream, three slots of request and
+  // reply buffers, and per slot the events copy-in done / scan done / copy-out done
+  cudaStream_t copy_stream = nullptr;
+  uint8_t* d_pipe = nullptr;
+  uint64_t pipe_cap = 0;
+  cudaEvent_t pipe_ev[9] = {nullptr};
   tpir_bloom_state bloom;
 };
 

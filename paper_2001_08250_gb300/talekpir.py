@@ -87,6 +87,7 @@ _SIGS = [
     ("tpir_read_batch", ctypes.c_int, [_vp, _vp, _u32, _vp]),
     ("tpir_read_batch_async", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp]),
     ("tpir_read_batch_masked", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp]),
+    ("tpir_read_batch_pipelined", ctypes.c_int, [_vp, _vp, _u64, _u32, _vp]),
     ("tpir_read_batch_masked_async", ctypes.c_int, [_vp, _vp, _u32, _vp, _vp, _vp]),
     ("tpir_mask_generate", ctypes.c_int, [_vp, _u32, _u64, _vp, _vp]),
     ("tpir_xor_combine", ctypes.c_int, [_vp, _u32, _u64, _vp, _vp]),
@@ -282,6 +283,19 @@ class DB:
             out = np.empty((B, self.row_bytes), dtype=np.uint8)
         assert out.flags["C_CONTIGUOUS"] and out.nbytes == B * self.row_bytes
         _check(lib().tpir_read_batch(self.h, _hptr(r), B, _hptr(out)), "tpir_read_batch")
+        return out
+
+    def read_batch_pipelined(self, req_bits: np.ndarray, batch: int,
+                             out: np.ndarray | None = None) -> np.ndarray:
+        """Synchronous read of many request rows (host) in batches whose copies
+        overlap the scans."""
+        r = np.ascontiguousarray(req_bits, dtype=np.uint64).reshape(-1, self.words64)
+        B = r.shape[0]
+        if out is None:
+            out = np.empty((B, self.row_bytes), dtype=np.uint8)
+        assert out.flags["C_CONTIGUOUS"] and out.nbytes == B * self.row_bytes
+        _check(lib().tpir_read_batch_pipelined(self.h, _hptr(r), B, int(batch), _hptr(out)),
+               "tpir_read_batch_pipelined")
         return out
 
     def read_batch_async(self, d_req, B: int, d_out, stream=None) -> None:

@@ -294,3 +294,24 @@ def test_tensor_kernel_exact_counts_all_ones(n, B):
         got = db.read_batch(R)
     assert (got == exp[None, :]).all()
     assert talekpir.device_status() == talekpir.OK
+
+
+@pytest.mark.parametrize("B_total,batch,kernel", [(1000, 256, 0), (37, 256, 0), (513, 128, TENSOR),
+                                                  (300, 7, PLAIN), (257, 64, BATCHED), (600, 200, M4RM)])
+def test_pipelined_host_reads_bit_exact(B_total, batch, kernel):
+    """The pipelined host-buffer read (copies overlapping the scans over three
+    rotating device slots) gives the oracle's replies for every request, with
+    a ragged last batch and a batch larger than the request set."""
+    torch = require_cuda()
+    n, d, z = 3000, 4, 1024
+    T = synth.table_bytes(n, d, z, seed=101)
+    R = synth.random_bits(B_total, n, seed=102, table=B_total)
+    hR = torch.from_numpy(R.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    hO = torch.empty((B_total, d * z), dtype=torch.uint8).pin_memory().numpy()
+    with _db(n, d, z, T) as db:
+        db.set_kernel(kernel)
+        got = db.read_batch_pipelined(hR, batch, hO)
+        assert np.array_equal(got, oracle.read_batch(T, n, d, z, R))
+        # pageable buffers give the same replies (the copies just do not overlap)
+        assert np.array_equal(db.read_batch_pipelined(R, batch), got)
+    assert talekpir.device_status() == talekpir.OK
