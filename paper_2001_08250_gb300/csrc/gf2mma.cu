@@ -494,43 +494,61 @@ __global__ void __launch_bounds__(kGThreads, 1)
           bool ok = true;
           if (r >= L.nbuf)
             ok = mb::wait_sleep(&acce[buf], ((r / L.nbuf) - 1u) & 1u, abort_flag, status, kGWaitNs, 64);
-          for (uint64_t ks = it.k0; ok && ks < it.k1; ks += kGKStage, ++iter) {
-            // stage slot and phase of iteration iter, kept incrementally
-            const uint32_t s = is, ph = iph;
+          // The tensor pipe queues almost nothing beyond the MMA it runs, so
+          // the issuer's time between stages is idle tensor time: it checks
+          // the next stage's barrier while the current stage's second-to-last
+          // MMA runs (when it would wait to issue anyway), then issues the
+          // last MMA, commits the stage and goes straight on.
+          bool have = ok;
+          if (have) {
+            have = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          ok = have;
+          for (uint64_t ks = it.k0; have; ks += kGKStage, ++iter) {
+            const uint32_t s = is;
             if (++is == kGStages) {
               is = 0;
               iph ^= 1u;
             }
-            // the stage is normally full already: a plain test first, the
-            // bounded wait only when it is not
-            if (!mb::test(&full[s], ph) && !mb::wait(&full[s], ph, abort_flag, status, kGWaitNs)) {
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool more = ks + kGKStage < it.k1;
             // descriptors: the stage's bases plus constant K-step offsets (a
             // single issuing thread is latency-bound: building descriptors
             // from addresses before every MMA halved the tensor pipe's rate)
             const uint64_t sa = adesc0 + s * kDescStage, sb = bdesc0 + s * kDescStage;
             const uint32_t acc0 = ks > it.k0 ? 1u : 0u;
             const uint64_t left = it.k1 - ks;
-            if (left >= kGKStage && it.mt == 2) {
+            const uint32_t nk = left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
+            const uint32_t total = nk * it.mt;  // MMAs of the stage: (K-step, tile) pairs
+            if (total == 8) {
 #pragma unroll
-              for (uint32_t j = 0; j < 4; ++j) {
-                g_mma(acc, sa + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
-                g_mma(acc + 256u, sa + kDescTile + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
-              }
-            } else if (left >= kGKStage) {
+              for (uint32_t q = 0; q < 7; ++q)
+                g_mma(acc + 256u * (q & 1u), sa + kDescTile * (q & 1u) + kDescKa * (q >> 1),
+                      sb + kDescKb * (q >> 1), (q >> 1) ? 1u : acc0);
+            } else if (total == 4 && it.mt == 1) {
 #pragma unroll
-              for (uint32_t j = 0; j < 4; ++j) g_mma(acc, sa + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+              for (uint32_t q = 0; q < 3; ++q) g_mma(acc, sa + kDescKa * q, sb + kDescKb * q, q ? 1u : acc0);
             } else {
-              const uint32_t nk = static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
-              for (uint32_t j = 0; j < nk; ++j)
-                for (uint32_t t = 0; t < it.mt; ++t)
-                  g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j,
-                        j ? 1u : acc0);
+              for (uint32_t q = 0; q + 1 < total; ++q) {
+                const uint32_t j = q / it.mt, t = q % it.mt;
+                g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+              }
+            }
+            bool next_ok = true;
+            if (more) {
+              next_ok = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            {
+              const uint32_t q = total - 1, j = q / it.mt, t = q % it.mt;
+              g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
             }
             g_commit(&empty[s]);
+            if (!more) break;
+            if (!next_ok) {
+              ok = false;
+              break;
+            }
           }
           if (ok) g_commit(&accf[buf]);
         }
