@@ -466,7 +466,8 @@ def main() -> None:
         line = {
             "metric": "pir_reads_per_s", "value": value, "unit": "reads/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "e4m3 0/1 operands, fp32 exact integer counts (replies u8, bit-exact)",
             "data": "synthetic", "config": workload_config(args),
             "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": ck,
