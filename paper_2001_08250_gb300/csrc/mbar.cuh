@@ -28,11 +28,13 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
           saddr(bar))
       : "memory");
 }
+// The thread sleeps in try_wait until the phase completes or about a
+// millisecond passes (the suspend-time hint), instead of spinning.
 __device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, 1000000;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(saddr(bar)), "r"(parity)
