@@ -11,8 +11,8 @@
 // row, block of up to 256 requests = two M-tiles of 128, k-chunk of buckets).
 // The MMA is M = 128 requests x N = 256 columns x K = 32 buckets.
 //
-// Data flow per CTA (persistent, one per SM, 416 threads):
-//   warp 12     streams the strip (8 words of 128 rows per stage) with 2-D TMA
+// Data flow per CTA (persistent, one per SM, 576 threads):
+//   warp 16     streams the strip (8 words of 128 rows per stage) with 2-D TMA
 //               loads into a 6-deep ring of raw stages, ahead of use;
 //   warps 0-3   table producers: each takes 32 rows of a raw stage, one row
 //               per lane, and writes the row's 256 bits as e4m3 bytes (a set
@@ -22,11 +22,14 @@
 //   warps 4-7   request producers: expand each request's 128 bits of the
 //               stage into the other operand (the next stage's words are
 //               loaded while the current one is expanded);
-//   warp 8 lane 0 issues the MMAs of each stage into the item's accumulators
+//   warp 17 lane 0 issues the MMAs of each stage into the item's accumulators
 //               and commits them to the stage's "empty" barrier;
-//   warps 8-11  epilogue: read the accumulators (tcgen05.ld), take each sum's
+//   warps 8-15  epilogue: read the accumulators (tcgen05.ld), take each sum's
 //               parity, and store (single k-chunk) or XOR-reduce (split, or a
-//               masked read) the reply words.
+//               masked read) the reply words; two groups of four warps split
+//               an item (one M-tile, or half the strip's words, each), so the
+//               tensor pipe waits half as long when one item's accumulators
+//               fill the tensor memory.
 // Stages: 3 x 64 KiB ring (A: 2 x 128 requests x 128 buckets, K-major; B:
 // 256 columns x 128 buckets, MN-major).  Accumulators: 2 x 256 TMEM columns (two M-tiles of one
 // item, or two items of one M-tile each, double-buffered).  Every wait is
@@ -58,7 +61,8 @@ constexpr int kGSbo = (kGKStage / 16) * 128;     // A: bytes between 8-row core-
 constexpr int kGLbo = 128;                       // A: bytes between 16-byte K chunks
 constexpr int kGSboB = (kGKStage / 8) * 128;     // B: bytes between 16-column groups
 constexpr int kGLboB = 128;                      // B: bytes between 8-bucket K groups
-constexpr int kGThreads = 416;
+constexpr int kGThreads = 576;                   // 18 warps (roles in the kernel)
+constexpr uint32_t kGTmaWarp = 16, kGIssueWarp = 17;
 constexpr int kGRaw = 6;                         // raw table stages in flight
 constexpr int kGRawBytes = 128 * kGWords * 4;    // 128 rows x 8 words: 4 KiB
 constexpr int kGSmem = 1024 + kGStages * kGStageBytes + kGRaw * kGRawBytes;
@@ -310,6 +314,42 @@ __device__ __forceinline__ void g_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Parity words of NC consecutive table words (w0 ..) for request b from the
+// accumulator columns at taddr, written (or XOR-reduced, for a split k range
+// or masked replies) into the reply row.  Reply rows are whole 16-byte words.
+template <int NC>
+__device__ __forceinline__ void g_epilogue(const GJob& J, uint32_t taddr, uint32_t b, uint32_t w0) {
+  uint32_t pw[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    pw[c] = 0u;
+    if (w0 + c < J.Wd) {  // uniform across the warp
+      uint32_t v[32];
+      g_ld32(taddr + 32u * c, v);
+      pw[c] = g_parity_word(v);
+    }
+  }
+  if (b >= J.B) return;
+  uint32_t* o = J.out + static_cast<uint64_t>(b) * J.Wd + w0;
+  if (J.split) {
+#pragma unroll
+    for (int c = 0; c < NC; c += 2) {
+      if (w0 + c + 1 < J.Wd)
+        g_red_xor64(o + c, pw[c], pw[c + 1]);
+      else if (w0 + c < J.Wd)
+        atomicXor(o + c, pw[c]);
+    }
+  } else if (w0 + NC <= J.Wd) {
+#pragma unroll
+    for (int c = 0; c < NC; c += 4)
+      reinterpret_cast<uint4*>(o)[c / 4] = make_uint4(pw[c], pw[c + 1], pw[c + 2], pw[c + 3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (w0 + c < J.Wd) o[c] = pw[c];
+  }
+}
+
 // One stage of the request operand: waits for the stage slot, writes this
 // thread's request in each M-tile (128 bits of the stage as e4m3 bytes,
 // K-major) and marks its part of the stage full.  False if the CTA aborted.
@@ -365,7 +405,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mb::init(&accf[b], kGIssuers);
-      mb::init(&acce[b], 128);
+      mb::init(&acce[b], 256);
     }
     mb::init(&drain, kGIssuers);
     for (int s = 0; s < kGRaw; ++s) {
@@ -387,7 +427,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
-  if (warp == 12) {
+  if (warp == kGTmaWarp) {
     // ------------------------- table strip loads (TMA) -------------------------
     if (lane == 0) {
       uint32_t p = 0;
@@ -476,90 +516,98 @@ __global__ void __launch_bounds__(kGThreads, 1)
       g_cur_next(cc, L);
       g_req_load(L, cc, q, xc);
     }
-  } else {
-    // ------------------------- MMA issue + epilogue -------------------------
-    const uint32_t ew = warp - 8;  // tensor-memory lanes 32 ew .. 32 ew + 31
-    const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc_b(stage0 + 2 * kGTile);
-    const uint32_t lag = L.nbuf - 1;
-    uint32_t iter = 0, is = 0, iph = 0;  // issuer: stage count, slot, phase
-    bool pdl_waited = false;
-    for (uint32_t r = 0;; ++r) {
-      const uint32_t item = g_item_of(r);
-      const bool issue = item < L.total_items;
-      if (warp == 8) {
-        if (issue && lane == 0 && !*abort_flag) {
-          const GItem it = g_decode(L, item);
-          const uint32_t buf = L.nbuf == 2 ? (r & 1u) : 0u;
-          const uint32_t acc = tmem + buf * 256u;
-          bool ok = true;
-          if (r >= L.nbuf)
-            ok = mb::wait_sleep(&acce[buf], ((r / L.nbuf) - 1u) & 1u, abort_flag, status, kGWaitNs, 64);
-          // The tensor pipe queues almost nothing beyond the MMA it runs, so
-          // the issuer's time between stages is idle tensor time: it checks
-          // the next stage's barrier while the current stage's second-to-last
-          // MMA runs (when it would wait to issue anyway), then issues the
-          // last MMA, commits the stage and goes straight on.
-          bool have = ok;
-          if (have) {
-            have = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  } else if (warp == kGIssueWarp) {
+    // ------------------------- MMA issue (one thread) -------------------------
+    if (lane == 0) {
+      const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc_b(stage0 + 2 * kGTile);
+      uint32_t iter = 0, is = 0, iph = 0;  // stage count, slot, phase
+      for (uint32_t r = 0;; ++r) {
+        const uint32_t item = g_item_of(r);
+        if (item >= L.total_items || *abort_flag) break;
+        const GItem it = g_decode(L, item);
+        const uint32_t buf = L.nbuf == 2 ? (r & 1u) : 0u;
+        const uint32_t acc = tmem + buf * 256u;
+        bool ok = true;
+        if (r >= L.nbuf)
+          ok = mb::wait_sleep(&acce[buf], ((r / L.nbuf) - 1u) & 1u, abort_flag, status, kGWaitNs, 64);
+        // The tensor pipe queues almost nothing beyond the MMA it runs, so
+        // the issuer's time between stages is idle tensor time: it checks
+        // the next stage's barrier while the current stage's second-to-last
+        // MMA runs (when it would wait to issue anyway), then issues the
+        // last MMA, commits the stage and goes straight on.
+        bool have = ok;
+        if (have) {
+          have = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        ok = have;
+        for (uint64_t ks = it.k0; have; ks += kGKStage, ++iter) {
+          const uint32_t s = is;
+          if (++is == kGStages) {
+            is = 0;
+            iph ^= 1u;
           }
-          ok = have;
-          for (uint64_t ks = it.k0; have; ks += kGKStage, ++iter) {
-            const uint32_t s = is;
-            if (++is == kGStages) {
-              is = 0;
-              iph ^= 1u;
-            }
-            const bool more = ks + kGKStage < it.k1;
-            // descriptors: the stage's bases plus constant K-step offsets (a
-            // single issuing thread is latency-bound: building descriptors
-            // from addresses before every MMA halved the tensor pipe's rate)
-            const uint64_t sa = adesc0 + s * kDescStage, sb = bdesc0 + s * kDescStage;
-            const uint32_t acc0 = ks > it.k0 ? 1u : 0u;
-            const uint64_t left = it.k1 - ks;
-            const uint32_t nk = left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
-            const uint32_t total = nk * it.mt;  // MMAs of the stage: (K-step, tile) pairs
-            if (total == 8) {
+          const bool more = ks + kGKStage < it.k1;
+          // descriptors: the stage's bases plus constant K-step offsets (a
+          // single issuing thread is latency-bound: building descriptors
+          // from addresses before every MMA halved the tensor pipe's rate)
+          const uint64_t sa = adesc0 + s * kDescStage, sb = bdesc0 + s * kDescStage;
+          const uint32_t acc0 = ks > it.k0 ? 1u : 0u;
+          const uint64_t left = it.k1 - ks;
+          const uint32_t nk = left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
+          const uint32_t total = nk * it.mt;  // MMAs of the stage: (K-step, tile) pairs
+          if (total == 8) {
 #pragma unroll
-              for (uint32_t q = 0; q < 7; ++q)
-                g_mma(acc + 256u * (q & 1u), sa + kDescTile * (q & 1u) + kDescKa * (q >> 1),
-                      sb + kDescKb * (q >> 1), (q >> 1) ? 1u : acc0);
-            } else if (total == 4 && it.mt == 1) {
+            for (uint32_t q = 0; q < 7; ++q)
+              g_mma(acc + 256u * (q & 1u), sa + kDescTile * (q & 1u) + kDescKa * (q >> 1),
+                    sb + kDescKb * (q >> 1), (q >> 1) ? 1u : acc0);
+          } else if (total == 4 && it.mt == 1) {
 #pragma unroll
-              for (uint32_t q = 0; q < 3; ++q) g_mma(acc, sa + kDescKa * q, sb + kDescKb * q, q ? 1u : acc0);
-            } else {
-              for (uint32_t q = 0; q + 1 < total; ++q) {
-                const uint32_t j = q / it.mt, t = q % it.mt;
-                g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
-              }
-            }
-            bool next_ok = true;
-            if (more) {
-              next_ok = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            }
-            {
-              const uint32_t q = total - 1, j = q / it.mt, t = q % it.mt;
+            for (uint32_t q = 0; q < 3; ++q) g_mma(acc, sa + kDescKa * q, sb + kDescKb * q, q ? 1u : acc0);
+          } else {
+            for (uint32_t q = 0; q + 1 < total; ++q) {
+              const uint32_t j = q / it.mt, t = q % it.mt;
               g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
             }
-            g_commit(&empty[s]);
-            if (!more) break;
-            if (!next_ok) {
-              ok = false;
-              break;
-            }
           }
-          if (ok) g_commit(&accf[buf]);
+          bool next_ok = true;
+          if (more) {
+            next_ok = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          {
+            const uint32_t q = total - 1, j = q / it.mt, t = q % it.mt;
+            g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+          }
+          g_commit(&empty[s]);
+          if (!more) break;
+          if (!next_ok) {
+            ok = false;
+            break;
+          }
         }
-        __syncwarp();
+        if (!ok) break;
+        g_commit(&accf[buf]);
       }
-      if (r < lag) {
-        if (!issue) break;
-        continue;
+      // Drain: every MMA issued completes before the tensor memory is freed
+      // (a no-op wait on the normal path; bounded on an aborted one).
+      g_commit(&drain);
+      const uint64_t t0 = mb::gtimer();
+      while (!mb::try_wait(&drain, 0)) {
+        if (mb::gtimer() - t0 > kGWaitNs) {
+          atomicExch(status, static_cast<int>(TPIR_ETIMEDOUT));
+          break;
+        }
       }
-      // epilogue of item e
-      const uint32_t e = r - lag;
+    }
+  } else if (warp >= 8 && warp < 16) {
+    // ------------------------------ epilogue ------------------------------
+    // Warp w reads tensor-memory lanes 32 (w % 4) .. + 31; the two groups of
+    // four warps take one M-tile each, or one half of the strip's words when
+    // the item has a single M-tile.
+    const uint32_t quarter = warp & 3u, half = (warp - 8) >> 2;
+    bool pdl_waited = false;
+    for (uint32_t e = 0;; ++e) {
       const uint32_t eitem = g_item_of(e);
       if (eitem >= L.total_items || *abort_flag) break;
       const GItem it = g_decode(L, eitem);
@@ -571,56 +619,19 @@ __global__ void __launch_bounds__(kGThreads, 1)
         pdl_waited = true;
       }
       const GJob& J = L.jobs[it.job];
-      const uint32_t w0 = it.strip * kGWords;
-      for (uint32_t t = 0; t < it.mt; ++t) {
-        const uint32_t b = it.b0 + 128u * t + 32u * ew + lane;
-        uint32_t pw[kGWords];
-#pragma unroll
-        for (int c = 0; c < kGWords; ++c) {
-          pw[c] = 0u;
-          if (w0 + c < J.Wd) {  // uniform across the warp
-            uint32_t v[32];
-            g_ld32(tmem + buf * 256u + 256u * t + 32u * c + ((32u * ew) << 16), v);
-            pw[c] = g_parity_word(v);
-          }
-        }
-        if (b < J.B) {
-          uint32_t* o = J.out + static_cast<uint64_t>(b) * J.Wd + w0;
-          if (J.split) {
-#pragma unroll
-            for (int c = 0; c < kGWords; c += 2) {
-              if (w0 + c + 1 < J.Wd)
-                g_red_xor64(o + c, pw[c], pw[c + 1]);
-              else if (w0 + c < J.Wd)
-                atomicXor(o + c, pw[c]);
-            }
-          } else if (w0 + kGWords <= J.Wd) {
-            reinterpret_cast<uint4*>(o)[0] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
-            reinterpret_cast<uint4*>(o)[1] = make_uint4(pw[4], pw[5], pw[6], pw[7]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < kGWords; ++c)
-              if (w0 + c < J.Wd) o[c] = pw[c];
-          }
-        }
+      const uint32_t lanes = (32u * quarter) << 16;
+      if (it.mt == 2) {
+        g_epilogue<kGWords>(J, tmem + lanes + 256u * half, it.b0 + 128u * half + 32u * quarter + lane,
+                            it.strip * kGWords);
+      } else {
+        g_epilogue<kGWords / 2>(J, tmem + lanes + buf * 256u + 32u * (kGWords / 2) * half,
+                                it.b0 + 32u * quarter + lane, it.strip * kGWords + (kGWords / 2) * half);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mb::arrive(&acce[buf]);
     }
   }
 
-  // Drain: every MMA this CTA issued completes before its tensor memory is
-  // freed (a no-op wait on the normal path; bounded on an aborted one).
-  if (warp == 8 && lane == 0) {
-    g_commit(&drain);
-    const uint64_t t0 = mb::gtimer();
-    while (!mb::try_wait(&drain, 0)) {
-      if (mb::gtimer() - t0 > kGWaitNs) {
-        atomicExch(status, static_cast<int>(TPIR_ETIMEDOUT));
-        break;
-      }
-    }
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
