@@ -63,8 +63,10 @@ constexpr int kGSboB = (kGKStage / 8) * 128;     // B: bytes between 16-column g
 constexpr int kGLboB = 128;                      // B: bytes between 8-bucket K groups
 constexpr int kGThreads = 576;                   // 18 warps (roles in the kernel)
 constexpr uint32_t kGTmaWarp = 16, kGIssueWarp = 17;
-constexpr int kGRaw = 6;                         // raw table stages in flight
-constexpr int kGRawBytes = 128 * kGWords * 4;    // 128 rows x 8 words: 4 KiB
+constexpr int kGRaw = 4;                         // raw stages in flight
+constexpr int kGRawTable = 128 * kGWords * 4;    // table strip: 128 rows x 8 words, 4 KiB
+constexpr int kGRawReq = 256 * 16;               // request words: 256 requests x 128 bits
+constexpr int kGRawBytes = kGRawTable + kGRawReq;
 constexpr int kGSmem = 1024 + kGStages * kGStageBytes + kGRaw * kGRawBytes;
 constexpr uint32_t kGTmemCols = 512;
 constexpr uint64_t kGWaitNs = 4000000000ull;
@@ -92,6 +94,7 @@ struct GJob {
   uint64_t n;
   uint32_t Wd, words64, B;
   uint32_t n_strips, n_mb, kc_rows;
+  uint32_t stages;       // stages (kGKStage buckets) per strip: ceil(n / kGKStage)
   uint32_t item_begin;   // index of this job's first item in the launch
   uint32_t split;        // replies are initialised first and XOR-reduced into
 };
@@ -102,7 +105,12 @@ template <int NJ>
 struct GLaunch {
   CUtensorMap maps[NJ];
   GJob jobs[NJ];
-  uint32_t njobs, total_items, nbuf, pad;
+  uint32_t njobs, total_items, nbuf;
+  uint32_t span;     // one-job launch cut into equal spans of stages (else items)
+  uint32_t req_tma;  // one-job launch: request words staged by TMA (rmap)
+  uint32_t req_box;  // rows of the request box: min(B, 256)
+  uint64_t units;    // span mode: stages of the whole job (M-blocks x strips x stages)
+  CUtensorMap rmap;  // request rows as 64-bit words (words64 x B), box 2 words x 256 rows
 };
 static_assert(sizeof(GLaunch<TPIR_MAX_JOBS>) <= 32000, "kernel parameters must stay below 32 KB");
 
@@ -147,37 +155,76 @@ __device__ __forceinline__ uint32_t g_item_of(uint32_t r) {
   return c + r * gridDim.x;
 }
 
-// Position in this CTA's sequence of stages (item r, stage start ks); every
-// role walks the same sequence.
+// This CTA's items in order.  Item mode: items c, ... of the launch list
+// (g_item_of).  Span mode (one job): the job's stages, ordered (M-block,
+// strip, stage), are cut into one contiguous span per CTA of equal length,
+// and an item is a run of the span within one strip and one k-chunk of
+// kGMaxCount buckets (chunks aligned to multiples of kGMaxCount), so a CTA
+// runs about two items (two accumulator read-outs) instead of one per
+// k-chunk, and every CTA does the same number of MMAs.
+struct GWalk {
+  uint64_t u, end;  // span mode: next stage unit, end of this CTA's span
+  uint32_t r;       // item mode: next round
+};
+template <int NJ>
+__device__ __forceinline__ GWalk g_walk_start(const GLaunch<NJ>& L) {
+  GWalk w;
+  w.r = 0;
+  w.u = L.units * blockIdx.x / gridDim.x;
+  w.end = L.units * (blockIdx.x + 1) / gridDim.x;
+  return w;
+}
+// The next item of this CTA into it; false when there is none.
+template <int NJ>
+__device__ __forceinline__ bool g_walk_next(const GLaunch<NJ>& L, GWalk& w, GItem& it) {
+  if (NJ == 1 && L.span) {
+    if (w.u >= w.end) return false;
+    const GJob& J = L.jobs[0];
+    const uint64_t per_mb = static_cast<uint64_t>(J.n_strips) * J.stages;
+    const uint64_t rem = w.u % per_mb;
+    const uint32_t mb = static_cast<uint32_t>(w.u / per_mb);
+    const uint64_t kst = rem % J.stages;
+    constexpr uint64_t kChunk = kGMaxCount / kGKStage;  // stages per k-chunk
+    const uint64_t lim = min(w.end, min(w.u - kst + J.stages, w.u - kst % kChunk + kChunk));
+    it.job = 0;
+    it.strip = static_cast<uint32_t>(rem / J.stages);
+    it.k0 = kst * kGKStage;
+    it.k1 = min(J.n, (kst + (lim - w.u)) * kGKStage);
+    it.b0 = mb * 256u;
+    it.mt = J.B - it.b0 > 128u ? 2u : 1u;
+    w.u = lim;
+    return true;
+  }
+  const uint32_t item = g_item_of(w.r++);
+  if (item >= L.total_items) return false;
+  it = g_decode(L, item);
+  return true;
+}
+
+// Position in this CTA's sequence of stages (its current item, stage start
+// ks); every role walks the same sequence.
 struct GCursor {
-  uint32_t r;
+  GWalk w;
   uint64_t ks;
   GItem it;
   bool valid;
 };
 template <int NJ>
 __device__ __forceinline__ void g_cur_item(GCursor& c, const GLaunch<NJ>& L) {
-  const uint32_t item = g_item_of(c.r);
-  c.valid = item < L.total_items;
-  if (c.valid) {
-    c.it = g_decode(L, item);
-    c.ks = c.it.k0;
-  }
+  c.valid = g_walk_next(L, c.w, c.it);
+  if (c.valid) c.ks = c.it.k0;
 }
 template <int NJ>
 __device__ __forceinline__ GCursor g_cur_start(const GLaunch<NJ>& L) {
   GCursor c;
-  c.r = 0;
+  c.w = g_walk_start(L);
   g_cur_item(c, L);
   return c;
 }
 template <int NJ>
 __device__ __forceinline__ void g_cur_next(GCursor& c, const GLaunch<NJ>& L) {
   c.ks += kGKStage;
-  if (c.ks >= c.it.k1) {
-    ++c.r;
-    g_cur_item(c, L);
-  }
+  if (c.ks >= c.it.k1) g_cur_item(c, L);
 }
 
 // Shared-memory matrix descriptors without swizzle.  K-major (A): 8-row x
@@ -232,13 +279,10 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
   return v;
 }
 
-// 2-D TMA load of a box (8 words x 128 rows at word x, row y) into shared
-// memory, completing `bytes` on the mbarrier
+// 2-D TMA load of a box at (x, y) into shared memory, completing its bytes
+// on the mbarrier (whose expected transaction count the caller has raised)
 __device__ __forceinline__ void g_tma_load(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                           uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb::saddr(bar)),
-               "r"(bytes)
-               : "memory");
+                                           uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
       "{%2, %3}], [%4];" ::"r"(dst),
@@ -410,7 +454,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     mb::init(&drain, kGIssuers);
     for (int s = 0; s < kGRaw; ++s) {
       mb::init(&raw_full[s], 1);
-      mb::init(&raw_empty[s], 4);
+      mb::init(&raw_empty[s], L.req_tma ? 8 : 4);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -434,8 +478,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
       for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++p) {
         const uint32_t rs = p % kGRaw, ph = (p / kGRaw) & 1u;
         if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
-        g_tma_load(raw0 + rs * kGRawBytes, &L.maps[c.it.job], static_cast<int>(c.it.strip * kGWords),
-                   static_cast<int>(c.ks), &raw_full[rs], kGRawBytes);
+        const uint32_t dst = raw0 + rs * kGRawBytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         mb::saddr(&raw_full[rs])),
+                     "r"(kGRawTable + (L.req_tma ? L.req_box * 16u : 0u))
+                     : "memory");
+        g_tma_load(dst, &L.maps[c.it.job], static_cast<int>(c.it.strip * kGWords),
+                   static_cast<int>(c.ks), &raw_full[rs]);
+        // the stage's 128 request bits of the item's 256 requests (rows past
+        // the batch read as zeros)
+        if (L.req_tma)
+          g_tma_load(dst + kGRawTable, &L.rmap, static_cast<int>(c.ks >> 6), static_cast<int>(c.it.b0),
+                     &raw_full[rs]);
       }
       // Loads still landing (an aborted run) complete before the CTA exits: a
       // slot has at most one load in flight, its latest, so its phase parity
@@ -487,6 +541,27 @@ __global__ void __launch_bounds__(kGThreads, 1)
       if (lane == 0) mb::arrive(&raw_empty[rs]);
       mb::arrive(&full[s]);
     }
+  } else if (warp < 8 && L.req_tma) {
+    // ------------------- request expanders (TMA-staged words) -------------------
+    // The TMA warp lands each stage's request words next to its table rows:
+    // thread q takes requests q and 128 + q of the item's 256 with one
+    // shared load each (a strided global load per request and stage would
+    // cost the load/store pipe a wavefront per thread).
+    const uint32_t q = threadIdx.x - 128u;
+    uint32_t iter = 0;
+    for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter) {
+      const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
+      if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) break;
+      const uint32_t ra = raw0 + rs * kGRawBytes + kGRawTable + q * 16u;
+      const uint4 v0 = ld_shared_v4(ra), v1 = ld_shared_v4(ra + 128u * 16u);
+      const uint64_t x[4] = {v0.x | static_cast<uint64_t>(v0.y) << 32, v0.z | static_cast<uint64_t>(v0.w) << 32,
+                             v1.x | static_cast<uint64_t>(v1.y) << 32, v1.z | static_cast<uint64_t>(v1.w) << 32};
+      // g_req_stage consumes the words (operand stores, then a proxy fence)
+      // before the slot is released
+      if (!g_req_stage(L, c, x, iter, q, stage0, full, empty, abort_flag, status)) break;
+      __syncwarp();
+      if (lane == 0) mb::arrive(&raw_empty[rs]);
+    }
   } else if (warp < 8) {
     // ------------------------ request expanders ------------------------
     // Three register sets, each loaded three stages ahead of its use, so a
@@ -521,10 +596,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (lane == 0) {
       const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc_b(stage0 + 2 * kGTile);
       uint32_t iter = 0, is = 0, iph = 0;  // stage count, slot, phase
+      GWalk w = g_walk_start(L);
       for (uint32_t r = 0;; ++r) {
-        const uint32_t item = g_item_of(r);
-        if (item >= L.total_items || *abort_flag) break;
-        const GItem it = g_decode(L, item);
+        GItem it;
+        if (*abort_flag || !g_walk_next(L, w, it)) break;
         const uint32_t buf = L.nbuf == 2 ? (r & 1u) : 0u;
         const uint32_t acc = tmem + buf * 256u;
         bool ok = true;
@@ -607,10 +682,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // the item has a single M-tile.
     const uint32_t quarter = warp & 3u, half = (warp - 8) >> 2;
     bool pdl_waited = false;
+    GWalk w = g_walk_start(L);
     for (uint32_t e = 0;; ++e) {
-      const uint32_t eitem = g_item_of(e);
-      if (eitem >= L.total_items || *abort_flag) break;
-      const GItem it = g_decode(L, eitem);
+      GItem it;
+      if (*abort_flag || !g_walk_next(L, w, it)) break;
       const uint32_t buf = L.nbuf == 2 ? (e & 1u) : 0u;
       if (!mb::wait_sleep(&accf[buf], (e / L.nbuf) & 1u, abort_flag, status, kGWaitNs, 256)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -678,6 +753,34 @@ cudaError_t g_table_map(const uint32_t* T, uint64_t n, uint32_t Wd, CUtensorMap*
   return cudaSuccess;
 }
 
+// Tensor map of a request block as a 2-D array of 64-bit words (words64 x B),
+// box 2 words x min(B, 256) rows: one stage's 128 bits of an item's requests.
+// Needs 16-byte aligned rows (R aligned, words64 even).
+cudaError_t g_req_map(const uint64_t* R, uint32_t words64, uint32_t B, CUtensorMap* out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::mutex mu;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q{};
+      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                       cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+  }
+  const cuuint64_t dims[2] = {words64, B};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(words64) * 8};
+  const cuuint32_t box[2] = {2, std::min<cuuint32_t>(B, 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(R), dims,
+                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Initialises the replies of the jobs that XOR-reduce into them (zeros, or
 // the masks of a masked job) before the scan: grid.y = job.  PDL-chained like
 // the scan, it waits for the previous kernel before writing.
@@ -704,6 +807,7 @@ GJob g_job(const uint64_t* R, uint32_t words64, uint32_t B, uint32_t* out, const
   j.B = B;
   j.n_strips = (Wd + kGWords - 1) / kGWords;
   j.n_mb = (B + 255) / 256;
+  j.stages = static_cast<uint32_t>((n + kGKStage - 1) / kGKStage);
   return j;
 }
 
@@ -733,7 +837,8 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (any) e = launch_pdl(gf2_init_kernel<NJ>, dim3(64, L.njobs), dim3(256), 0, st, L);
   if (e != cudaSuccess) return e;
-  const uint32_t grid = std::min<uint32_t>(L.total_items, device_sm_count());
+  const uint64_t work = L.span ? L.units : L.total_items;
+  const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(work, device_sm_count()));
   return launch_pdl(gf2_mma_kernel<NJ>, dim3(grid), dim3(kGThreads), kGSmem, st, L, status);
 }
 
@@ -747,38 +852,26 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
   L.njobs = 1;
   GJob J = g_job(R, words64, B, out, seeds, n, Wd);
   L.nbuf = B <= 128 ? 2u : 1u;
-  const int grid = device_sm_count();
-  // k-chunks minimising rounds x item time on the grid; item time ~ MMAs
-  // (128 cycles each at N = 256, K = 32) + epilogue, which the second
-  // accumulator hides when an item holds one M-tile
-  const double mts = B <= 128 ? 1.0 : 2.0;
-  const double epi = L.nbuf == 2 ? 600.0 : 2500.0;
-  const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
-  const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
-  double best = 1e300;
-  uint64_t best_rows = kGKStage;
-  for (uint64_t c = std::max<uint64_t>(1, min_kc); c <= std::max<uint64_t>(min_kc, std::min<uint64_t>(max_kc, 512)); ++c) {
-    const uint64_t rows = g_clamp_rows((n + c - 1) / c, n);
-    const uint64_t kcs = (n + rows - 1) / rows;
-    const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
-    const uint64_t rounds = (items + grid - 1) / grid;
-    const double cost = static_cast<double>(rounds) *
-                        (static_cast<double>(rows) / kGKStep * mts * 128.0 + epi);
-    if (cost < best) {
-      best = cost;
-      best_rows = rows;
-    }
-  }
-  J.kc_rows = static_cast<uint32_t>(best_rows);
-  const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;
-  const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
-  if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  // span mode: equal runs of stages per CTA; partial strips of several CTAs
+  // XOR-reduce into replies initialised first
+  L.span = 1;
+  J.kc_rows = static_cast<uint32_t>(kGMaxCount);
+  L.units = static_cast<uint64_t>(J.n_mb) * J.n_strips * J.stages;
+  if (L.units > (1ull << 48)) return cudaErrorInvalidValue;
   J.item_begin = 0;
-  J.split = (kcs > 1 || seeds) ? 1u : 0u;
+  J.split = 1;
   L.jobs[0] = J;
-  L.total_items = static_cast<uint32_t>(items);
+  L.total_items = 0;
   cudaError_t e = g_table_map(T, n, Wd, &L.maps[0]);
   if (e != cudaSuccess) return e;
+  // request words by TMA where the rows are 16-byte aligned (the box's x
+  // coordinate, a stage's first word, is even)
+  if ((reinterpret_cast<uintptr_t>(R) & 15u) == 0 && (words64 & 1u) == 0) {
+    if (g_req_map(R, words64, B, &L.rmap) == cudaSuccess) {
+      L.req_tma = 1;
+      L.req_box = std::min<uint32_t>(B, 256);
+    }
+  }
   return g_launch<1>(L, st);
 }
 

@@ -296,6 +296,30 @@ def test_tensor_kernel_exact_counts_all_ones(n, B):
     assert talekpir.device_status() == talekpir.OK
 
 
+@pytest.mark.parametrize("n,B", [(1024, 200), (4096, 96), (40000, 257), (4097, 300)])
+def test_tensor_kernel_request_rows_staged_or_loaded(n, B):
+    """Request rows 16-byte aligned with an even number of words are staged
+    into shared memory by TMA; rows at an 8-byte offset (or an odd word
+    count, n = 4097) are loaded by the expander threads.  Both give the
+    oracle's replies, for batches below, at and past one 256-request block."""
+    require_cuda()
+    d, z = 2, 256
+    T = synth.table_bytes(n, d, z, seed=31, table=n)
+    R = synth.random_bits(B, n, seed=32, table=n)
+    exp = oracle.read_batch(T, n, d, z, R)
+    with _db(n, d, z, T) as db:
+        db.set_kernel(TENSOR)
+        dO = dev_out(B, d * z)
+        dR = to_dev(R)
+        db.read_batch_async(dR, B, dO)
+        assert np.array_equal(to_host(dO), exp)
+        flat = to_dev(np.concatenate([np.zeros(1, np.uint64), R.reshape(-1)]))
+        dO.zero_()
+        db.read_batch_async(flat[1:], B, dO)  # rows 8 bytes off a 16-byte boundary
+        assert np.array_equal(to_host(dO), exp)
+    assert talekpir.device_status() == talekpir.OK
+
+
 @pytest.mark.parametrize("B_total,batch,kernel", [(1000, 256, 0), (37, 256, 0), (513, 128, TENSOR),
                                                   (300, 7, PLAIN), (257, 64, BATCHED), (600, 200, M4RM)])
 def test_pipelined_host_reads_bit_exact(B_total, batch, kernel):
