@@ -97,22 +97,23 @@ struct GJob {
   uint32_t stages;       // stages (kGKStage buckets) per strip: ceil(n / kGKStage)
   uint32_t item_begin;   // index of this job's first item in the launch
   uint32_t split;        // replies are initialised first and XOR-reduced into
+  uint32_t req_tma;      // request words staged by TMA (rows 16-byte aligned)
+  uint32_t req_box;      // rows of the request box: min(B, 256)
 };
 
-// A launch: NJ jobs (one for a single-table read), each with the tensor map of
-// its table, in the kernel parameters.
+// A launch: NJ jobs (one for a single-table read), each with the tensor maps
+// of its table and (req_tma) of its request rows, in the kernel parameters.
 template <int NJ>
 struct GLaunch {
   CUtensorMap maps[NJ];
+  CUtensorMap rmaps[NJ];  // request rows as 64-bit words (words64 x B), box 2 words x req_box rows
   GJob jobs[NJ];
   uint32_t njobs, total_items, nbuf;
-  uint32_t span;     // one-job launch cut into equal spans of stages (else items)
-  uint32_t req_tma;  // one-job launch: request words staged by TMA (rmap)
-  uint32_t req_box;  // rows of the request box: min(B, 256)
-  uint64_t units;    // span mode: stages of the whole job (M-blocks x strips x stages)
-  CUtensorMap rmap;  // request rows as 64-bit words (words64 x B), box 2 words x 256 rows
+  uint32_t span;   // one-job launch cut into equal spans of stages (else items)
+  uint64_t units;  // span mode: stages of the whole job (M-blocks x strips x stages)
 };
-static_assert(sizeof(GLaunch<TPIR_MAX_JOBS>) <= 32000, "kernel parameters must stay below 32 KB");
+constexpr int kGMultiJobs = 64;  // jobs per many-table launch (kernel parameter space)
+static_assert(sizeof(GLaunch<kGMultiJobs>) <= 32000, "kernel parameters must stay below 32 KB");
 
 struct GItem {
   uint32_t job, strip, b0, mt;
@@ -426,7 +427,37 @@ __device__ __forceinline__ bool g_req_stage(const GLaunch<NJ>& L, const GCursor&
   return true;
 }
 
-template <int NJ>
+// One stage of a request expander: the stage's words (RM = 1: from the raw
+// stage, else the preloaded x), the operand (g_req_stage), then (RM = 1) the
+// raw slot's release.  False if the CTA aborted.
+template <int NJ, int RM>
+__device__ __forceinline__ bool g_req_step(const GLaunch<NJ>& L, const GCursor& c,
+                                           const uint64_t (&x)[4], uint32_t iter, uint32_t q,
+                                           uint32_t lane, uint32_t stage0, uint32_t raw0,
+                                           uint64_t* full, uint64_t* empty, uint64_t* raw_full,
+                                           uint64_t* raw_empty, volatile int* abort_flag,
+                                           int* status) {
+  if constexpr (RM == 0) {
+    return g_req_stage(L, c, x, iter, q, stage0, full, empty, abort_flag, status);
+  } else {
+    const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
+    if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) return false;
+    const uint32_t ra = raw0 + rs * kGRawBytes + kGRawTable + q * 16u;
+    const uint4 v0 = ld_shared_v4(ra), v1 = ld_shared_v4(ra + 128u * 16u);
+    const uint64_t y[4] = {v0.x | static_cast<uint64_t>(v0.y) << 32, v0.z | static_cast<uint64_t>(v0.w) << 32,
+                           v1.x | static_cast<uint64_t>(v1.y) << 32, v1.z | static_cast<uint64_t>(v1.w) << 32};
+    // the words are consumed (operand stores, then a proxy fence) before
+    // the slot is released
+    if (!g_req_stage(L, c, y, iter, q, stage0, full, empty, abort_flag, status)) return false;
+    __syncwarp();
+    if (lane == 0) mb::arrive(&raw_empty[rs]);
+    return true;
+  }
+}
+
+// RM: how the request words reach the request expanders: 0 = per-thread
+// global loads, 1 = staged by TMA (every job's rows 16-byte aligned).
+template <int NJ, int RM>
 __global__ void __launch_bounds__(kGThreads, 1)
     gf2_mma_kernel(const __grid_constant__ GLaunch<NJ> L, int* status) {
   extern __shared__ uint8_t smem_raw[];
@@ -454,7 +485,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     mb::init(&drain, kGIssuers);
     for (int s = 0; s < kGRaw; ++s) {
       mb::init(&raw_full[s], 1);
-      mb::init(&raw_empty[s], L.req_tma ? 8 : 4);
+      mb::init(&raw_empty[s], RM == 0 ? 4 : 8);  // table (+ request) expander warps
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -479,17 +510,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const uint32_t rs = p % kGRaw, ph = (p / kGRaw) & 1u;
         if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
         const uint32_t dst = raw0 + rs * kGRawBytes;
+        constexpr bool rq = RM == 1;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                          mb::saddr(&raw_full[rs])),
-                     "r"(kGRawTable + (L.req_tma ? L.req_box * 16u : 0u))
+                     "r"(kGRawTable + (rq ? L.jobs[c.it.job].req_box * 16u : 0u))
                      : "memory");
         g_tma_load(dst, &L.maps[c.it.job], static_cast<int>(c.it.strip * kGWords),
                    static_cast<int>(c.ks), &raw_full[rs]);
         // the stage's 128 request bits of the item's 256 requests (rows past
         // the batch read as zeros)
-        if (L.req_tma)
-          g_tma_load(dst + kGRawTable, &L.rmap, static_cast<int>(c.ks >> 6), static_cast<int>(c.it.b0),
-                     &raw_full[rs]);
+        if (rq)
+          g_tma_load(dst + kGRawTable, &L.rmaps[c.it.job], static_cast<int>(c.ks >> 6),
+                     static_cast<int>(c.it.b0), &raw_full[rs]);
       }
       // Loads still landing (an aborted run) complete before the CTA exits: a
       // slot has at most one load in flight, its latest, so its phase parity
@@ -541,31 +573,24 @@ __global__ void __launch_bounds__(kGThreads, 1)
       if (lane == 0) mb::arrive(&raw_empty[rs]);
       mb::arrive(&full[s]);
     }
-  } else if (warp < 8 && L.req_tma) {
+  } else if (warp < 8 && RM == 1) {
     // ------------------- request expanders (TMA-staged words) -------------------
-    // The TMA warp lands each stage's request words next to its table rows:
-    // thread q takes requests q and 128 + q of the item's 256 with one
-    // shared load each (a strided global load per request and stage would
-    // cost the load/store pipe a wavefront per thread).
+    // Thread q takes requests q and 128 + q of the item's (up to) 256: the TMA
+    // warp lands each stage's request words next to its table rows, one shared
+    // load per request and stage (a strided global load per request and stage
+    // would cost the load/store pipe a wavefront per thread).
     const uint32_t q = threadIdx.x - 128u;
     uint32_t iter = 0;
-    for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter) {
-      const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
-      if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) break;
-      const uint32_t ra = raw0 + rs * kGRawBytes + kGRawTable + q * 16u;
-      const uint4 v0 = ld_shared_v4(ra), v1 = ld_shared_v4(ra + 128u * 16u);
-      const uint64_t x[4] = {v0.x | static_cast<uint64_t>(v0.y) << 32, v0.z | static_cast<uint64_t>(v0.w) << 32,
-                             v1.x | static_cast<uint64_t>(v1.y) << 32, v1.z | static_cast<uint64_t>(v1.w) << 32};
-      // g_req_stage consumes the words (operand stores, then a proxy fence)
-      // before the slot is released
-      if (!g_req_stage(L, c, x, iter, q, stage0, full, empty, abort_flag, status)) break;
-      __syncwarp();
-      if (lane == 0) mb::arrive(&raw_empty[rs]);
-    }
+    const uint64_t none[4] = {0, 0, 0, 0};
+    for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter)
+      if (!g_req_step<NJ, 1>(L, c, none, iter, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
+                             abort_flag, status))
+        break;
   } else if (warp < 8) {
     // ------------------------ request expanders ------------------------
-    // Three register sets, each loaded three stages ahead of its use, so a
-    // stage never waits on the request words' (L2) latency.
+    // Thread q takes requests q and 128 + q of the item's (up to) 256, loaded
+    // from global memory into three register sets, each loaded three stages
+    // ahead of its use so that a stage does not wait on their (L2) latency.
     const uint32_t q = threadIdx.x - 128u;
     GCursor ca = g_cur_start(L);
     GCursor cb = ca;
@@ -578,15 +603,24 @@ __global__ void __launch_bounds__(kGThreads, 1)
     g_req_load(L, cc, q, xc);
     uint32_t iter = 0;
     for (;;) {
-      if (!ca.valid || !g_req_stage(L, ca, xa, iter++, q, stage0, full, empty, abort_flag, status)) break;
+      if (!ca.valid ||
+          !g_req_step<NJ, RM>(L, ca, xa, iter++, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
+                      abort_flag, status))
+        break;
       ca = cc;
       g_cur_next(ca, L);
       g_req_load(L, ca, q, xa);
-      if (!cb.valid || !g_req_stage(L, cb, xb, iter++, q, stage0, full, empty, abort_flag, status)) break;
+      if (!cb.valid ||
+          !g_req_step<NJ, RM>(L, cb, xb, iter++, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
+                      abort_flag, status))
+        break;
       cb = ca;
       g_cur_next(cb, L);
       g_req_load(L, cb, q, xb);
-      if (!cc.valid || !g_req_stage(L, cc, xc, iter++, q, stage0, full, empty, abort_flag, status)) break;
+      if (!cc.valid ||
+          !g_req_step<NJ, RM>(L, cc, xc, iter++, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
+                      abort_flag, status))
+        break;
       cc = cb;
       g_cur_next(cc, L);
       g_req_load(L, cc, q, xc);
@@ -811,6 +845,17 @@ GJob g_job(const uint64_t* R, uint32_t words64, uint32_t B, uint32_t* out, const
   return j;
 }
 
+// Request words by TMA where the rows are 16-byte aligned (R aligned, words64
+// even: the box's x coordinate, a stage's first word, is then even too).
+bool g_stageable(const uint64_t* R, uint32_t words64);
+void g_set_req(GJob& j, CUtensorMap* rmap) {
+  j.req_tma = 0;
+  if (g_stageable(j.R, j.words64) && g_req_map(j.R, j.words64, j.B, rmap) == cudaSuccess) {
+    j.req_tma = 1;
+    j.req_box = std::min<uint32_t>(j.B, 256);
+  }
+}
+
 // k-chunks of kc_rows buckets: a multiple of a stage, at most kGMaxCount (a
 // k-chunk's counts stay in the range in which the fp32 accumulators were
 // checked exact, whatever the tensor cores' internal accumulation width)
@@ -821,11 +866,11 @@ uint32_t g_clamp_rows(uint64_t rows, uint64_t n) {
   return static_cast<uint32_t>(std::min<uint64_t>(rows, kGMaxCount));
 }
 
-template <int NJ>
+template <int NJ, int RM>
 cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
   static bool ready = false;
   if (!ready) {
-    cudaError_t e = cudaFuncSetAttribute(gf2_mma_kernel<NJ>,
+    cudaError_t e = cudaFuncSetAttribute(gf2_mma_kernel<NJ, RM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
     if (e != cudaSuccess) return e;
     ready = true;
@@ -839,7 +884,7 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const uint64_t work = L.span ? L.units : L.total_items;
   const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(work, device_sm_count()));
-  return launch_pdl(gf2_mma_kernel<NJ>, dim3(grid), dim3(kGThreads), kGSmem, st, L, status);
+  return launch_pdl(gf2_mma_kernel<NJ, RM>, dim3(grid), dim3(kGThreads), kGSmem, st, L, status);
 }
 
 }  // namespace
@@ -860,24 +905,24 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
   if (L.units > (1ull << 48)) return cudaErrorInvalidValue;
   J.item_begin = 0;
   J.split = 1;
+  g_set_req(J, &L.rmaps[0]);
   L.jobs[0] = J;
   L.total_items = 0;
   cudaError_t e = g_table_map(T, n, Wd, &L.maps[0]);
   if (e != cudaSuccess) return e;
-  // request words by TMA where the rows are 16-byte aligned (the box's x
-  // coordinate, a stage's first word, is even)
-  if ((reinterpret_cast<uintptr_t>(R) & 15u) == 0 && (words64 & 1u) == 0) {
-    if (g_req_map(R, words64, B, &L.rmap) == cudaSuccess) {
-      L.req_tma = 1;
-      L.req_box = std::min<uint32_t>(B, 256);
-    }
-  }
-  return g_launch<1>(L, st);
+  return J.req_tma ? g_launch<1, 1>(L, st) : g_launch<1, 0>(L, st);
 }
 
-cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
-  if (count == 0) return cudaSuccess;
-  if (count > TPIR_MAX_JOBS) return cudaErrorInvalidValue;
+namespace {
+
+// Request rows that TMA can stage: 16-byte aligned with an even word count.
+bool g_stageable(const uint64_t* R, uint32_t words64) {
+  return (reinterpret_cast<uintptr_t>(R) & 15u) == 0 && (words64 & 1u) == 0;
+}
+
+// One persistent launch for up to kGMultiJobs jobs, all with staged request
+// words (staged) or all with per-thread loads.
+cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, bool staged, cudaStream_t st) {
   const int grid = device_sm_count();
   // items of about equal cost (bucket rows x M-tiles), ~8 per CTA; jobs in
   // descending item cost, assigned round-robin to the CTAs
@@ -909,7 +954,7 @@ cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStre
   std::vector<size_t> order(js.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-  GLaunch<TPIR_MAX_JOBS> L{};
+  GLaunch<kGMultiJobs> L{};
   L.njobs = 0;
   L.nbuf = all_small ? 2u : 1u;
   uint64_t items = 0;
@@ -921,10 +966,34 @@ cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStre
     if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
     cudaError_t e = g_table_map(src[oi]->T, j.n, j.Wd, &L.maps[L.njobs]);
     if (e != cudaSuccess) return e;
+    if (staged) {
+      g_set_req(j, &L.rmaps[L.njobs]);
+      if (!j.req_tma) return cudaErrorInvalidValue;
+    }
     L.jobs[L.njobs++] = j;
   }
   L.total_items = static_cast<uint32_t>(items);
-  return g_launch<TPIR_MAX_JOBS>(L, st);
+  return staged ? g_launch<kGMultiJobs, 1>(L, st) : g_launch<kGMultiJobs, 0>(L, st);
+}
+
+}  // namespace
+
+cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
+  if (count > TPIR_MAX_JOBS) return cudaErrorInvalidValue;
+  // the jobs whose request words TMA stages, then the others, in launches
+  // of at most kGMultiJobs jobs (the kernel parameters hold two tensor maps
+  // per job), in stream order
+  for (int staged = 1; staged >= 0; --staged) {
+    std::vector<M4Request> part;
+    for (uint32_t i = 0; i < count; ++i)
+      if (reqs[i].B && g_stageable(reqs[i].R, reqs[i].words64) == (staged != 0)) part.push_back(reqs[i]);
+    for (size_t i = 0; i < part.size(); i += kGMultiJobs) {
+      const uint32_t c = static_cast<uint32_t>(std::min<size_t>(kGMultiJobs, part.size() - i));
+      const cudaError_t e = g_launch_multi(part.data() + i, c, staged != 0, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace tpir

@@ -156,6 +156,48 @@ def test_multi_table_one_launch_bit_exact():
     assert talekpir.device_status() == talekpir.OK
 
 
+def test_multi_table_tensor_launch_chunks_and_request_paths():
+    """More tables than one tensor-core launch holds (its parameters carry
+    two tensor maps per table, 64 tables per launch): 100 small tables of
+    >= 96 requests, forced to the tensor-core kernel, with even and odd
+    request-word counts and every third request block at an 8-byte offset
+    (per-thread loads instead of TMA staging), read in one call and from a
+    captured graph; every reply bit-exact."""
+    torch = require_cuda()
+    rng = np.random.default_rng(90)
+    dbs, jobs, exp, keep = [], [], [], []
+    for i in range(100):
+        n = int(rng.integers(60, 400))
+        d, z, B = int(rng.choice([1, 2])), int(rng.choice([32, 64, 256])), int(rng.integers(96, 300))
+        T = synth.table_bytes(n, d, z, seed=91, table=i)
+        R = synth.random_bits(B, n, seed=92, table=i)
+        db = _db(n, d, z, T)
+        db.set_kernel(TENSOR)
+        dbs.append(db)
+        if i % 3 == 0:
+            flat = to_dev(np.concatenate([np.zeros(1, np.uint64), R.reshape(-1)]))
+            keep.append(flat)
+            dR = flat[1:]
+        else:
+            dR = to_dev(R)
+        jobs.append((db, B, dR, dev_out(B, d * z)))
+        exp.append(oracle.read_batch(T, n, d, z, R))
+    talekpir.read_multi_async(jobs)
+    for (db, B, dR, dO), e in zip(jobs, exp):
+        assert np.array_equal(to_host(dO), e)
+    g = talekpir.MultiGraph(jobs)
+    for (_, _, _, dO) in jobs:
+        dO.fill_(0xA5)
+    g.launch()
+    torch.cuda.synchronize()
+    for (db, B, dR, dO), e in zip(jobs, exp):
+        assert np.array_equal(to_host(dO), e)
+    g.close()
+    for db in dbs:
+        db.close()
+    assert talekpir.device_status() == talekpir.OK
+
+
 def test_large_table_gf2_product_sampled():
     """n = 2^20, d = 4, 1 KiB messages (4 GiB), B = 1024 packed request rows:
     sampled rows plus a Freivalds check of the whole product, for the batched
