@@ -95,6 +95,7 @@ struct GJob {
   uint32_t Wd, words64, B;
   uint32_t n_strips, n_mb, kc_rows;
   uint32_t stages;       // stages (kGKStage buckets) per strip: ceil(n / kGKStage)
+  uint32_t span_w;       // span mode: stages per block (the order of the units)
   uint32_t item_begin;   // index of this job's first item in the launch
   uint32_t split;        // replies are initialised first and XOR-reduced into
   uint32_t req_tma;      // request words staged by TMA (rows 16-byte aligned)
@@ -157,12 +158,14 @@ __device__ __forceinline__ uint32_t g_item_of(uint32_t r) {
 }
 
 // This CTA's items in order.  Item mode: items c, ... of the launch list
-// (g_item_of).  Span mode (one job): the job's stages, ordered (M-block,
-// strip, stage), are cut into one contiguous span per CTA of equal length,
-// and an item is a run of the span within one strip and one k-chunk of
-// kGMaxCount buckets (chunks aligned to multiples of kGMaxCount), so a CTA
-// runs about two items (two accumulator read-outs) instead of one per
-// k-chunk, and every CTA does the same number of MMAs.
+// (g_item_of).  Span mode (one job with at most about one k-chunk of stages
+// per CTA): the job's stages are ordered (M-block, block of span_w stages,
+// strip, stage) and cut into one contiguous span per CTA of equal length; an
+// item is a run of the span within one strip of one block and one k-chunk of
+// kGMaxCount buckets (chunks aligned to multiples of kGMaxCount).  With
+// span_w = all stages (strip-major) a CTA runs one or two items (accumulator
+// read-outs); with span_w about the span length the CTAs of one block read
+// the same rows, strip by strip, at about the same time.
 struct GWalk {
   uint64_t u, end;  // span mode: next stage unit, end of this CTA's span
   uint32_t r;       // item mode: next round
@@ -182,13 +185,26 @@ __device__ __forceinline__ bool g_walk_next(const GLaunch<NJ>& L, GWalk& w, GIte
     if (w.u >= w.end) return false;
     const GJob& J = L.jobs[0];
     const uint64_t per_mb = static_cast<uint64_t>(J.n_strips) * J.stages;
-    const uint64_t rem = w.u % per_mb;
+    const uint64_t o = w.u % per_mb;
     const uint32_t mb = static_cast<uint32_t>(w.u / per_mb);
-    const uint64_t kst = rem % J.stages;
+    const uint64_t W = J.span_w, nfull = J.stages / W;
+    const uint64_t full_units = nfull * J.n_strips * W;
+    uint64_t bw, b0, r;  // block width, first stage, unit within the block
+    if (o < full_units) {
+      bw = W;
+      b0 = o / (J.n_strips * W) * W;
+      r = o % (J.n_strips * W);
+    } else {
+      bw = J.stages - nfull * W;
+      b0 = nfull * W;
+      r = o - full_units;
+    }
+    const uint64_t st = r % bw;  // stage within the block
+    const uint64_t kst = b0 + st;
     constexpr uint64_t kChunk = kGMaxCount / kGKStage;  // stages per k-chunk
-    const uint64_t lim = min(w.end, min(w.u - kst + J.stages, w.u - kst % kChunk + kChunk));
+    const uint64_t lim = min(w.end, min(w.u - st + bw, w.u - kst % kChunk + kChunk));
     it.job = 0;
-    it.strip = static_cast<uint32_t>(rem / J.stages);
+    it.strip = static_cast<uint32_t>(r / bw);
     it.k0 = kst * kGKStage;
     it.k1 = min(J.n, (kst + (lim - w.u)) * kGKStage);
     it.b0 = mb * 256u;
@@ -897,17 +913,58 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
   L.njobs = 1;
   GJob J = g_job(R, words64, B, out, seeds, n, Wd);
   L.nbuf = B <= 128 ? 2u : 1u;
-  // span mode: equal runs of stages per CTA; partial strips of several CTAs
-  // XOR-reduce into replies initialised first
-  L.span = 1;
-  J.kc_rows = static_cast<uint32_t>(kGMaxCount);
-  L.units = static_cast<uint64_t>(J.n_mb) * J.n_strips * J.stages;
-  if (L.units > (1ull << 48)) return cudaErrorInvalidValue;
+  const uint64_t units = static_cast<uint64_t>(J.n_mb) * J.n_strips * J.stages;
+  if (units > (1ull << 48)) return cudaErrorInvalidValue;
+  const uint64_t grid = std::min<uint64_t>(units, device_sm_count());
+  const uint64_t per_cta = (units + grid - 1) / grid;
+  if (per_cta <= kGMaxCount / kGKStage) {
+    // span mode: equal runs of stages per CTA, strip-major (one block of
+    // all stages); partial strips of several CTAs XOR-reduce into replies
+    // initialised first.  Blocks of about one span (CTAs of a block reading
+    // the same rows together) cut DRAM reads of the paper-scale launch from
+    // 3x to 1.04x the table but took 7 % longer: the tail block's CTAs run
+    // several short items, and DRAM is not the bound here.
+    L.span = 1;
+    L.units = units;
+    J.kc_rows = static_cast<uint32_t>(kGMaxCount);
+    J.span_w = J.stages;
+    J.split = 1;
+    L.total_items = 0;
+  } else {
+    // item mode (long spans): items of whole k-chunks, taken round by round
+    // so that the CTAs of a round read the same rows; k-chunks minimise
+    // rounds x item time on the grid, item time ~ MMAs (128 cycles each at
+    // N = 256, K = 32) + epilogue, which the second accumulator hides when
+    // an item holds one M-tile
+    const double mts = B <= 128 ? 1.0 : 2.0;
+    const double epi = L.nbuf == 2 ? 600.0 : 2500.0;
+    const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
+    const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
+    double best = 1e300;
+    uint64_t best_rows = kGKStage;
+    for (uint64_t c = std::max<uint64_t>(1, min_kc);
+         c <= std::max<uint64_t>(min_kc, std::min<uint64_t>(max_kc, 512)); ++c) {
+      const uint64_t rows = g_clamp_rows((n + c - 1) / c, n);
+      const uint64_t kcs = (n + rows - 1) / rows;
+      const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
+      const uint64_t rounds = (items + grid - 1) / grid;
+      const double cost = static_cast<double>(rounds) *
+                          (static_cast<double>(rows) / kGKStep * mts * 128.0 + epi);
+      if (cost < best) {
+        best = cost;
+        best_rows = rows;
+      }
+    }
+    J.kc_rows = static_cast<uint32_t>(best_rows);
+    const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;
+    const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
+    if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+    J.split = (kcs > 1 || seeds) ? 1u : 0u;
+    L.total_items = static_cast<uint32_t>(items);
+  }
   J.item_begin = 0;
-  J.split = 1;
   g_set_req(J, &L.rmaps[0]);
   L.jobs[0] = J;
-  L.total_items = 0;
   cudaError_t e = g_table_map(T, n, Wd, &L.maps[0]);
   if (e != cudaSuccess) return e;
   return J.req_tma ? g_launch<1, 1>(L, st) : g_launch<1, 0>(L, st);
