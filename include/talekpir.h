@@ -201,7 +201,7 @@ tpir_status tpir_xor_combine(const void *const *d_srcs, uint32_t count, uint64_t
                              void *d_dst, void *stream);
 
 /* Force a kernel choice for tests and benchmarks: 0 = automatic (plain for
- * B <= 4, tensor-core for B >= 96 on rows of >= 256 bytes, register-tiled
+ * B <= 4, tensor-core for B >= 48 on rows of >= 256 bytes, register-tiled
  * batched otherwise), 1 = plain streaming kernel (B <= 4 per launch,
  * larger B is split into launches; TMA-staged where the row width allows),
  * 2 = batched register-tiled kernel, 3 = plain kernel with register
@@ -234,7 +234,7 @@ tpir_status tpir_tune_clear(void);
 
 /* Many tables in ONE persistent launch per kernel kind (the uneven-batching
  * workload): job i reads B_i rows of d_req_bits_i against db_i into d_out_i.
- * Tables may differ in n, d and msg_bytes.  Jobs of >= 96 requests on rows of
+ * Tables may differ in n, d and msg_bytes.  Jobs of >= 48 requests on rows of
  * >= 256 bytes share one launch of the tensor-core kernel, the others one
  * launch of the register-tiled kernel (a db forced to kernel 4 sends its jobs
  * to the Four-Russians kernel instead: one launch for jobs of up to 256

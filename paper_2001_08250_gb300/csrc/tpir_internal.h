@@ -175,7 +175,7 @@ cudaError_t launch_xor_combine(const uint4* const* srcs, uint32_t count, uint64_
 // wide: 512-request tiles (jobs of more than 256 requests), else 256
 cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, cudaStream_t st);
 constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel beats LOP3
-constexpr uint32_t kTensorMinB = 96;  // batch from which the tensor-core kernel beats LOP3
+constexpr uint32_t kTensorMinB = 48;  // batch from which the tensor-core kernel beats LOP3 (measured)
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
 // Rice coding of sparse bit vectors (rice.cu).
 struct RiceRequest {
