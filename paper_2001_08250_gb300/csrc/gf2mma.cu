@@ -13,15 +13,19 @@
 //
 // Data flow per CTA (persistent, one per SM, 576 threads):
 //   warp 16     streams the strip (8 words of 128 rows per stage) with 2-D TMA
-//               loads into a 6-deep ring of raw stages, ahead of use;
+//               loads into a ring of raw stages, ahead of use, and with them
+//               the stage's request words (2 words of each of the item's
+//               requests) when their rows can be staged: rows of an even
+//               number of 64-bit words as rows, of an odd number as row
+//               pairs (TMA boxes start 16-byte aligned);
 //   warps 0-3   table producers: each takes 32 rows of a raw stage, one row
 //               per lane, and writes the row's 256 bits as e4m3 bytes (a set
 //               bit = 2^-6) into the B operand, which is MN-major (columns
 //               contiguous), so a table row needs no transposition (buckets
 //               and columns take the shared order of g_spread);
 //   warps 4-7   request producers: expand each request's 128 bits of the
-//               stage into the other operand (the next stage's words are
-//               loaded while the current one is expanded);
+//               stage into the other operand, from the raw stage (staged
+//               rows) or from global memory three stages ahead;
 //   warp 17 lane 0 issues the MMAs of each stage into the item's accumulators
 //               and commits them to the stage's "empty" barrier;
 //   warps 8-15  epilogue: read the accumulators (tcgen05.ld), take each sum's
@@ -63,11 +67,20 @@ constexpr int kGSboB = (kGKStage / 8) * 128;     // B: bytes between 16-column g
 constexpr int kGLboB = 128;                      // B: bytes between 8-bucket K groups
 constexpr int kGThreads = 576;                   // 18 warps (roles in the kernel)
 constexpr uint32_t kGTmaWarp = 16, kGIssueWarp = 17;
-constexpr int kGRaw = 4;                         // raw stages in flight
 constexpr int kGRawTable = 128 * kGWords * 4;    // table strip: 128 rows x 8 words, 4 KiB
-constexpr int kGRawReq = 256 * 16;               // request words: 256 requests x 128 bits
-constexpr int kGRawBytes = kGRawTable + kGRawReq;
-constexpr int kGSmem = 1024 + kGStages * kGStageBytes + kGRaw * kGRawBytes;
+// Raw stages (table strip + request words) by request-staging mode RM:
+// RM = 0 or 1: 256 request rows x 16 bytes; RM = 2 (rows of an odd number
+// of words, staged as row pairs): 128 even rows x 16 bytes, then 128 odd
+// rows x 32 bytes (a 4-word box from the even word before the stage's two).
+template <int RM>
+__host__ __device__ constexpr int g_raw_req() { return RM == 2 ? 128 * 16 + 128 * 32 : 256 * 16; }
+template <int RM>
+__host__ __device__ constexpr int g_raw_stages() { return RM == 2 ? 3 : 4; }
+template <int RM>
+__host__ __device__ constexpr int g_raw_bytes() { return kGRawTable + g_raw_req<RM>(); }
+template <int RM>
+__host__ __device__ constexpr int g_smem() { return 1024 + kGStages * kGStageBytes + g_raw_stages<RM>() * g_raw_bytes<RM>(); }
+static_assert(g_smem<1>() <= 232448 && g_smem<2>() <= 232448, "dynamic shared memory above 227 KiB");
 constexpr uint32_t kGTmemCols = 512;
 constexpr uint64_t kGWaitNs = 4000000000ull;
 constexpr int kGIssuers = 1;                     // MMA-issuing threads
@@ -98,8 +111,9 @@ struct GJob {
   uint32_t span_w;       // span mode: stages per block (the order of the units)
   uint32_t item_begin;   // index of this job's first item in the launch
   uint32_t split;        // replies are initialised first and XOR-reduced into
-  uint32_t req_tma;      // request words staged by TMA (rows 16-byte aligned)
-  uint32_t req_box;      // rows of the request box: min(B, 256)
+  uint32_t req_tma;      // request words staged by TMA: 0 no, 1 rows, 2 row pairs
+  uint32_t req_box;      // rows of the request box (RM 1: min(B, 256); RM 2: even rows)
+  uint32_t req_box_o;    // RM 2: rows of the odd-row box (0: B = 1, no odd rows)
 };
 
 // A launch: NJ jobs (one for a single-table read), each with the tensor maps
@@ -107,7 +121,8 @@ struct GJob {
 template <int NJ>
 struct GLaunch {
   CUtensorMap maps[NJ];
-  CUtensorMap rmaps[NJ];  // request rows as 64-bit words (words64 x B), box 2 words x req_box rows
+  CUtensorMap rmaps[NJ];    // request rows (RM 1) or even rows (RM 2) as 64-bit words
+  CUtensorMap rmaps_o[NJ];  // RM 2: row pairs as 64-bit words (odd rows' boxes)
   GJob jobs[NJ];
   uint32_t njobs, total_items, nbuf;
   uint32_t span;   // one-job launch cut into equal spans of stages (else items)
@@ -287,6 +302,12 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
                : "memory");
 }
 
+__device__ __forceinline__ uint2 ld_shared_v2(uint32_t addr) {
+  uint2 v;
+  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
   uint4 v;
   asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
@@ -453,15 +474,32 @@ __device__ __forceinline__ bool g_req_step(const GLaunch<NJ>& L, const GCursor& 
                                            uint64_t* full, uint64_t* empty, uint64_t* raw_full,
                                            uint64_t* raw_empty, volatile int* abort_flag,
                                            int* status) {
+  constexpr int kGRaw = g_raw_stages<RM>(), kGRawBytes = g_raw_bytes<RM>();
   if constexpr (RM == 0) {
     return g_req_stage(L, c, x, iter, q, stage0, full, empty, abort_flag, status);
   } else {
     const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
     if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) return false;
-    const uint32_t ra = raw0 + rs * kGRawBytes + kGRawTable + q * 16u;
-    const uint4 v0 = ld_shared_v4(ra), v1 = ld_shared_v4(ra + 128u * 16u);
-    const uint64_t y[4] = {v0.x | static_cast<uint64_t>(v0.y) << 32, v0.z | static_cast<uint64_t>(v0.w) << 32,
-                           v1.x | static_cast<uint64_t>(v1.y) << 32, v1.z | static_cast<uint64_t>(v1.w) << 32};
+    const uint32_t base = raw0 + rs * kGRawBytes + kGRawTable;
+    uint64_t y[4];
+    if constexpr (RM == 1) {
+      const uint4 v0 = ld_shared_v4(base + q * 16u), v1 = ld_shared_v4(base + (128u + q) * 16u);
+      y[0] = v0.x | static_cast<uint64_t>(v0.y) << 32;
+      y[1] = v0.z | static_cast<uint64_t>(v0.w) << 32;
+      y[2] = v1.x | static_cast<uint64_t>(v1.y) << 32;
+      y[3] = v1.z | static_cast<uint64_t>(v1.w) << 32;
+    } else {
+      // request 128 t + q of the block: even rows' words at their pair's 16
+      // bytes, odd rows' at bytes 8 .. 23 of their pair's 32
+#pragma unroll
+      for (uint32_t t = 0; t < 2; ++t) {
+        const uint32_t pr = 64u * t + (q >> 1);
+        const uint32_t a = (q & 1u) ? base + 128u * 16u + pr * 32u + 8u : base + pr * 16u;
+        const uint2 lo = ld_shared_v2(a), hi = ld_shared_v2(a + 8u);
+        y[2 * t] = lo.x | static_cast<uint64_t>(lo.y) << 32;
+        y[2 * t + 1] = hi.x | static_cast<uint64_t>(hi.y) << 32;
+      }
+    }
     // the words are consumed (operand stores, then a proxy fence) before
     // the slot is released
     if (!g_req_stage(L, c, y, iter, q, stage0, full, empty, abort_flag, status)) return false;
@@ -472,10 +510,13 @@ __device__ __forceinline__ bool g_req_step(const GLaunch<NJ>& L, const GCursor& 
 }
 
 // RM: how the request words reach the request expanders: 0 = per-thread
-// global loads, 1 = staged by TMA (every job's rows 16-byte aligned).
+// global loads, 1 = staged by TMA (every job's rows 16-byte aligned: an even
+// number of words), 2 = staged by TMA as row pairs (rows of an odd number of
+// words; the pairs are 16-byte aligned).
 template <int NJ, int RM>
 __global__ void __launch_bounds__(kGThreads, 1)
     gf2_mma_kernel(const __grid_constant__ GLaunch<NJ> L, int* status) {
+  constexpr int kGRaw = g_raw_stages<RM>(), kGRawBytes = g_raw_bytes<RM>();
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], accf[2], acce[2], drain;
   __shared__ __align__(8) uint64_t raw_full[kGRaw], raw_empty[kGRaw];
@@ -526,18 +567,29 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const uint32_t rs = p % kGRaw, ph = (p / kGRaw) & 1u;
         if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
         const uint32_t dst = raw0 + rs * kGRawBytes;
-        constexpr bool rq = RM == 1;
+        const GJob& J = L.jobs[c.it.job];
+        const uint32_t rbytes = RM == 1 ? J.req_box * 16u : RM == 2 ? J.req_box * 16u + J.req_box_o * 32u : 0u;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                          mb::saddr(&raw_full[rs])),
-                     "r"(kGRawTable + (rq ? L.jobs[c.it.job].req_box * 16u : 0u))
+                     "r"(kGRawTable + rbytes)
                      : "memory");
         g_tma_load(dst, &L.maps[c.it.job], static_cast<int>(c.it.strip * kGWords),
                    static_cast<int>(c.ks), &raw_full[rs]);
         // the stage's 128 request bits of the item's 256 requests (rows past
         // the batch read as zeros)
-        if (rq)
+        if constexpr (RM == 1) {
           g_tma_load(dst + kGRawTable, &L.rmaps[c.it.job], static_cast<int>(c.ks >> 6),
                      static_cast<int>(c.it.b0), &raw_full[rs]);
+        } else if constexpr (RM == 2) {
+          // row pairs: even rows' two words at word ks/64 of the pair, odd
+          // rows' four words from the word before theirs (even, so the box
+          // starts 16-byte aligned); words past the pair read as zeros
+          const int wi = static_cast<int>(c.ks >> 6), py = static_cast<int>(c.it.b0 >> 1);
+          g_tma_load(dst + kGRawTable, &L.rmaps[c.it.job], wi, py, &raw_full[rs]);
+          if (J.req_box_o)
+            g_tma_load(dst + kGRawTable + 128 * 16, &L.rmaps_o[c.it.job],
+                       static_cast<int>(J.words64) + wi - 1, py, &raw_full[rs]);
+        }
       }
       // Loads still landing (an aborted run) complete before the CTA exits: a
       // slot has at most one load in flight, its latest, so its phase parity
@@ -589,7 +641,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
       if (lane == 0) mb::arrive(&raw_empty[rs]);
       mb::arrive(&full[s]);
     }
-  } else if (warp < 8 && RM == 1) {
+  } else if (warp < 8 && RM != 0) {
     // ------------------- request expanders (TMA-staged words) -------------------
     // Thread q takes requests q and 128 + q of the item's (up to) 256: the TMA
     // warp lands each stage's request words next to its table rows, one shared
@@ -599,7 +651,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     uint32_t iter = 0;
     const uint64_t none[4] = {0, 0, 0, 0};
     for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter)
-      if (!g_req_step<NJ, 1>(L, c, none, iter, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
+      if (!g_req_step<NJ, RM>(L, c, none, iter, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
                              abort_flag, status))
         break;
   } else if (warp < 8) {
@@ -803,10 +855,10 @@ cudaError_t g_table_map(const uint32_t* T, uint64_t n, uint32_t Wd, CUtensorMap*
   return cudaSuccess;
 }
 
-// Tensor map of a request block as a 2-D array of 64-bit words (words64 x B),
-// box 2 words x min(B, 256) rows: one stage's 128 bits of an item's requests.
-// Needs 16-byte aligned rows (R aligned, words64 even).
-cudaError_t g_req_map(const uint64_t* R, uint32_t words64, uint32_t B, CUtensorMap* out) {
+// Tensor map of request words as a 2-D array of 64-bit words: dims x by y
+// rows stride_words apart, box bx words x by rows (zero fill outside).
+cudaError_t g_req_map(const uint64_t* R, uint64_t x, uint64_t y, uint64_t stride_words, uint32_t bx,
+                      uint32_t by, CUtensorMap* out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::mutex mu;
   {
@@ -820,9 +872,9 @@ cudaError_t g_req_map(const uint64_t* R, uint32_t words64, uint32_t B, CUtensorM
       encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
   }
-  const cuuint64_t dims[2] = {words64, B};
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(words64) * 8};
-  const cuuint32_t box[2] = {2, std::min<cuuint32_t>(B, 256)};
+  const cuuint64_t dims[2] = {x, y};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(stride_words) * 8};
+  const cuuint32_t box[2] = {bx, by};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(R), dims,
                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -861,15 +913,41 @@ GJob g_job(const uint64_t* R, uint32_t words64, uint32_t B, uint32_t* out, const
   return j;
 }
 
-// Request words by TMA where the rows are 16-byte aligned (R aligned, words64
-// even: the box's x coordinate, a stage's first word, is then even too).
-bool g_stageable(const uint64_t* R, uint32_t words64);
-void g_set_req(GJob& j, CUtensorMap* rmap) {
+// How TMA can stage a job's request words (0: it cannot, per-thread loads).
+// TMA boxes start 16-byte aligned: the x coordinate of a stage's first word
+// is even, so with R 16-byte aligned rows of an even number of words are
+// staged as rows (1: box 2 words x min(B, 256) rows at (word, request));
+// rows of an odd number of words as row pairs, 16-byte aligned (2): the even
+// rows' two words (x = word, pair rows of 2 words64 words, dims words64 x
+// ceil(B/2)), the odd rows' from the even word before theirs (x = words64 +
+// word - 1 in the pair, box 4 words, dims 2 words64 x floor(B/2), so no box
+// reaches past the last row).
+uint32_t g_req_mode(const uint64_t* R, uint32_t words64) {
+  if (reinterpret_cast<uintptr_t>(R) & 15u) return 0;
+  return (words64 & 1u) ? 2u : 1u;
+}
+void g_set_req(GJob& j, CUtensorMap* rmap, CUtensorMap* rmap_o) {
   j.req_tma = 0;
-  if (g_stageable(j.R, j.words64) && g_req_map(j.R, j.words64, j.B, rmap) == cudaSuccess) {
-    j.req_tma = 1;
+  const uint32_t mode = g_req_mode(j.R, j.words64);
+  if (mode == 1) {
+    if (g_req_map(j.R, j.words64, j.B, j.words64, 2, std::min<uint32_t>(j.B, 256), rmap) != cudaSuccess)
+      return;
     j.req_box = std::min<uint32_t>(j.B, 256);
+    j.req_box_o = 0;
+  } else if (mode == 2) {
+    const uint32_t ev = (j.B + 1) / 2, od = j.B / 2;
+    if (g_req_map(j.R, j.words64, ev, 2ull * j.words64, 2, std::min<uint32_t>(ev, 128), rmap) !=
+        cudaSuccess)
+      return;
+    if (od && g_req_map(j.R, 2ull * j.words64, od, 2ull * j.words64, 4, std::min<uint32_t>(od, 128),
+                        rmap_o) != cudaSuccess)
+      return;
+    j.req_box = std::min<uint32_t>(ev, 128);
+    j.req_box_o = std::min<uint32_t>(od, 128);
+  } else {
+    return;
   }
+  j.req_tma = mode;
 }
 
 // k-chunks of kc_rows buckets: a multiple of a stage, at most kGMaxCount (a
@@ -887,7 +965,7 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
   static bool ready = false;
   if (!ready) {
     cudaError_t e = cudaFuncSetAttribute(gf2_mma_kernel<NJ, RM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem<RM>());
     if (e != cudaSuccess) return e;
     ready = true;
   }
@@ -900,7 +978,7 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const uint64_t work = L.span ? L.units : L.total_items;
   const uint32_t grid = static_cast<uint32_t>(std::min<uint64_t>(work, device_sm_count()));
-  return launch_pdl(gf2_mma_kernel<NJ, RM>, dim3(grid), dim3(kGThreads), kGSmem, st, L, status);
+  return launch_pdl(gf2_mma_kernel<NJ, RM>, dim3(grid), dim3(kGThreads), g_smem<RM>(), st, L, status);
 }
 
 }  // namespace
@@ -963,23 +1041,20 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
     L.total_items = static_cast<uint32_t>(items);
   }
   J.item_begin = 0;
-  g_set_req(J, &L.rmaps[0]);
+  g_set_req(J, &L.rmaps[0], &L.rmaps_o[0]);
   L.jobs[0] = J;
   cudaError_t e = g_table_map(T, n, Wd, &L.maps[0]);
   if (e != cudaSuccess) return e;
-  return J.req_tma ? g_launch<1, 1>(L, st) : g_launch<1, 0>(L, st);
+  if (J.req_tma == 1) return g_launch<1, 1>(L, st);
+  if (J.req_tma == 2) return g_launch<1, 2>(L, st);
+  return g_launch<1, 0>(L, st);
 }
 
 namespace {
 
-// Request rows that TMA can stage: 16-byte aligned with an even word count.
-bool g_stageable(const uint64_t* R, uint32_t words64) {
-  return (reinterpret_cast<uintptr_t>(R) & 15u) == 0 && (words64 & 1u) == 0;
-}
-
-// One persistent launch for up to kGMultiJobs jobs, all with staged request
-// words (staged) or all with per-thread loads.
-cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, bool staged, cudaStream_t st) {
+// One persistent launch for up to kGMultiJobs jobs, all with request words
+// staged the same way (mode: g_req_mode).
+cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode, cudaStream_t st) {
   const int grid = device_sm_count();
   // items of about equal cost (bucket rows x M-tiles), ~8 per CTA; jobs in
   // descending item cost, assigned round-robin to the CTAs
@@ -1023,30 +1098,32 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, bool staged, c
     if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
     cudaError_t e = g_table_map(src[oi]->T, j.n, j.Wd, &L.maps[L.njobs]);
     if (e != cudaSuccess) return e;
-    if (staged) {
-      g_set_req(j, &L.rmaps[L.njobs]);
-      if (!j.req_tma) return cudaErrorInvalidValue;
+    if (mode) {
+      g_set_req(j, &L.rmaps[L.njobs], &L.rmaps_o[L.njobs]);
+      if (j.req_tma != mode) return cudaErrorInvalidValue;
     }
     L.jobs[L.njobs++] = j;
   }
   L.total_items = static_cast<uint32_t>(items);
-  return staged ? g_launch<kGMultiJobs, 1>(L, st) : g_launch<kGMultiJobs, 0>(L, st);
+  if (mode == 1) return g_launch<kGMultiJobs, 1>(L, st);
+  if (mode == 2) return g_launch<kGMultiJobs, 2>(L, st);
+  return g_launch<kGMultiJobs, 0>(L, st);
 }
 
 }  // namespace
 
 cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
   if (count > TPIR_MAX_JOBS) return cudaErrorInvalidValue;
-  // the jobs whose request words TMA stages, then the others, in launches
-  // of at most kGMultiJobs jobs (the kernel parameters hold two tensor maps
-  // per job), in stream order
-  for (int staged = 1; staged >= 0; --staged) {
+  // jobs grouped by how TMA stages their request words (rows, row pairs,
+  // per-thread loads), in launches of at most kGMultiJobs jobs (the kernel
+  // parameters hold three tensor maps per job), in stream order
+  for (uint32_t mode : {1u, 2u, 0u}) {
     std::vector<M4Request> part;
     for (uint32_t i = 0; i < count; ++i)
-      if (reqs[i].B && g_stageable(reqs[i].R, reqs[i].words64) == (staged != 0)) part.push_back(reqs[i]);
+      if (reqs[i].B && g_req_mode(reqs[i].R, reqs[i].words64) == mode) part.push_back(reqs[i]);
     for (size_t i = 0; i < part.size(); i += kGMultiJobs) {
       const uint32_t c = static_cast<uint32_t>(std::min<size_t>(kGMultiJobs, part.size() - i));
-      const cudaError_t e = g_launch_multi(part.data() + i, c, staged != 0, st);
+      const cudaError_t e = g_launch_multi(part.data() + i, c, mode, st);
       if (e != cudaSuccess) return e;
     }
   }
