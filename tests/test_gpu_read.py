@@ -362,6 +362,36 @@ def test_tensor_kernel_request_rows_staged_or_loaded(n, B):
     assert talekpir.device_status() == talekpir.OK
 
 
+@pytest.mark.parametrize("n,offset", [(4096, 0), (4160, 0), (4096, 1)])
+def test_tensor_kernel_back_to_back_launches(n, offset):
+    """Thirty launches of the tensor-core kernel back to back on one stream,
+    alternating two tables, in each request-staging mode (rows of 64 words
+    staged as rows, of 65 words as row pairs, and an 8-byte offset buffer
+    read by the expander threads): every reply of every launch bit-exact.
+    Catches ring-slot reuse races that a single launch can hide."""
+    torch = require_cuda()
+    d, z, B = 4, 256, 300
+    Ts = [synth.table_bytes(n, d, z, seed=41, table=t) for t in range(2)]
+    R = synth.random_bits(B, n, seed=42, table=n)
+    exps = [oracle.read_batch(T, n, d, z, R) for T in Ts]
+    dbs = [_db(n, d, z, T) for T in Ts]
+    for db in dbs:
+        db.set_kernel(TENSOR)
+    flat = to_dev(np.concatenate([np.zeros(offset, np.uint64), R.reshape(-1)]))
+    dR = flat[offset:]
+    outs = [dev_out(B, d * z) for _ in range(30)]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for i, o in enumerate(outs):
+            dbs[i % 2].read_batch_async(dR, B, o, s)
+    s.synchronize()
+    for i, o in enumerate(outs):
+        assert np.array_equal(to_host(o), exps[i % 2]), f"launch {i}"
+    for db in dbs:
+        db.close()
+    assert talekpir.device_status() == talekpir.OK
+
+
 @pytest.mark.parametrize("B_total,batch,kernel", [(1000, 256, 0), (37, 256, 0), (513, 128, TENSOR),
                                                   (300, 7, PLAIN), (257, 64, BATCHED), (600, 200, M4RM)])
 def test_pipelined_host_reads_bit_exact(B_total, batch, kernel):
