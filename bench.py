@@ -96,9 +96,11 @@ def alu_peak_tops(sm_mhz: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms during a region."""
+    """nvidia-smi clocks/throttle reasons sampled every 50 ms; stop() keeps the
+    samples whose timestamps fall in the timed region (all of the loaded run
+    if none do)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -110,12 +112,13 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
 
-    def stop(self) -> dict:
+    def stop(self, t_lo: float = 0.0, t_hi: float = 0.0) -> dict:
+        import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -124,23 +127,33 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in out.splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for name, v in zip(names, f[5:9]):
+        inside = [r for r in rows if r[0] is not None and t_lo <= r[0] <= t_hi]
+        window = "timed region"
+        if not inside:
+            inside, window = rows, "loaded run (warm-up and timed region)"
+        reasons = set()
+        for r in inside:
+            for name, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
+        sm = [r[1] for r in inside]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def dist_env():
@@ -283,17 +296,25 @@ def main() -> None:
                 events[i][1].record(stream)
 
     def timed(B, steps, warmup, with_launch_events=False, clocks=None, masked=False):
+        if clocks:
+            # the sampler starts while warm-up steps keep the GPU busy (at
+            # least 0.4 s of them), so its samples fall in the loaded run
+            clocks.start()
+        t_warm = time.perf_counter()
         with torch.cuda.stream(stream):
-            for _ in range(warmup):
+            done = 0
+            while done < warmup or (clocks and time.perf_counter() - t_warm < 0.4):
                 run_step(B, masked=masked)
+                done += 1
+                if clocks and done % 4 == 0:
+                    stream.synchronize()
         torch.cuda.synchronize()
         nb = (USERS + B - 1) // B
         ev = None
         per_launch = []
         barrier()
         torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
+        t_lo = time.time()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(stream)
         for _ in range(steps):
@@ -305,7 +326,7 @@ def main() -> None:
                 per_launch.append(ev)
         end.record(stream)
         torch.cuda.synchronize()
-        ck = clocks.stop() if clocks else None
+        ck = clocks.stop(t_lo, time.time()) if clocks else None
         barrier()
         ms = start.elapsed_time(end) / steps
         durs = [a.elapsed_time(b) for evs in per_launch for a, b in evs]

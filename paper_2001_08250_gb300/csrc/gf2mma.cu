@@ -344,7 +344,9 @@ __device__ __forceinline__ void g_req_load(const GLaunch<NJ>& L, const GCursor& 
     if (t < c.it.mt && b < J.B) {
       const uint64_t* rq = J.R + static_cast<uint64_t>(b) * J.words64;
       x[2 * t] = __ldg(rq + wi);
-      if (wi + 1 < J.words64) x[2 * t + 1] = __ldg(rq + wi + 1);
+      // the job's own words end at ceil(n / 64): a row shard's request rows
+      // are longer (words64 is the stride) and end with other shards' words
+      if (wi + 1 < (J.n + 63) / 64) x[2 * t + 1] = __ldg(rq + wi + 1);
     }
   }
 }
@@ -918,10 +920,10 @@ GJob g_job(const uint64_t* R, uint32_t words64, uint32_t B, uint32_t* out, const
 // is even, so with R 16-byte aligned rows of an even number of words are
 // staged as rows (1: box 2 words x min(B, 256) rows at (word, request));
 // rows of an odd number of words as row pairs, 16-byte aligned (2): the even
-// rows' two words (x = word, pair rows of 2 words64 words, dims words64 x
+// rows' two words (x = word, pair rows of 2 words64 words, dims nw x
 // ceil(B/2)), the odd rows' from the even word before theirs (x = words64 +
-// word - 1 in the pair, box 4 words, dims 2 words64 x floor(B/2), so no box
-// reaches past the last row).
+// word - 1 in the pair, box 4 words, dims words64 + nw x floor(B/2)), where
+// nw = ceil(n/64) are the job's own words of a row: no box reads past them.
 uint32_t g_req_mode(const uint64_t* R, uint32_t words64) {
   if (reinterpret_cast<uintptr_t>(R) & 15u) return 0;
   return (words64 & 1u) ? 2u : 1u;
@@ -929,17 +931,20 @@ uint32_t g_req_mode(const uint64_t* R, uint32_t words64) {
 void g_set_req(GJob& j, CUtensorMap* rmap, CUtensorMap* rmap_o) {
   j.req_tma = 0;
   const uint32_t mode = g_req_mode(j.R, j.words64);
+  // the job's own words of each row: ceil(n / 64) (a row shard's rows, words64
+  // apart, go on with other shards' words); boxes read zeros past them
+  const uint64_t nw = (j.n + 63) / 64;
   if (mode == 1) {
-    if (g_req_map(j.R, j.words64, j.B, j.words64, 2, std::min<uint32_t>(j.B, 256), rmap) != cudaSuccess)
+    if (g_req_map(j.R, nw, j.B, j.words64, 2, std::min<uint32_t>(j.B, 256), rmap) != cudaSuccess)
       return;
     j.req_box = std::min<uint32_t>(j.B, 256);
     j.req_box_o = 0;
   } else if (mode == 2) {
     const uint32_t ev = (j.B + 1) / 2, od = j.B / 2;
-    if (g_req_map(j.R, j.words64, ev, 2ull * j.words64, 2, std::min<uint32_t>(ev, 128), rmap) !=
+    if (g_req_map(j.R, nw, ev, 2ull * j.words64, 2, std::min<uint32_t>(ev, 128), rmap) !=
         cudaSuccess)
       return;
-    if (od && g_req_map(j.R, 2ull * j.words64, od, 2ull * j.words64, 4, std::min<uint32_t>(od, 128),
+    if (od && g_req_map(j.R, j.words64 + nw, od, 2ull * j.words64, 4, std::min<uint32_t>(od, 128),
                         rmap_o) != cudaSuccess)
       return;
     j.req_box = std::min<uint32_t>(ev, 128);
