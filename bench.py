@@ -50,8 +50,8 @@ TRAFFIC_BATCHED_B256 = (136.659968e6 + 3.284480e6 + 136.435200e6 + 0.130304e6 + 
 TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
 TRAFFIC_M4RM_B256 = (136.340736e6 + 3.074048e6 + 136.585216e6 + 0.072192e6 + 136.370944e6
                      + 0.116480e6) / 3
-TRAFFIC_GF2MMA_B256 = (403.978752e6 + 3.710208e6 + 397.036288e6 + 0.794112e6 + 395.130112e6
-                       + 0.936448e6) / 3
+TRAFFIC_GF2MMA_B256 = (406.219520e6 + 3.965440e6 + 401.490688e6 + 1.413888e6 + 395.858432e6
+                       + 1.180416e6) / 3
 
 
 def measured_peaks() -> dict:
