@@ -43,6 +43,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <vector>
 #include <mutex>
@@ -967,12 +968,13 @@ uint32_t g_clamp_rows(uint64_t rows, uint64_t n) {
 
 template <int NJ, int RM>
 cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
-  static bool ready = false;
-  if (!ready) {
+  // set once per process (idempotent, so threads racing here only repeat it)
+  static std::atomic<bool> ready{false};
+  if (!ready.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(gf2_mma_kernel<NJ, RM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem<RM>());
     if (e != cudaSuccess) return e;
-    ready = true;
+    ready.store(true, std::memory_order_release);
   }
   int* status = device_status_word();
   if (!status) return cudaErrorInvalidSymbol;

@@ -439,8 +439,8 @@ uint32_t m4_next_slot() {
 
 template <int MR, int NJ>
 cudaError_t m4_prepare() {
-  static bool ready = false;
-  if (ready) return cudaSuccess;
+  static std::atomic<bool> ready{false};  // idempotent set-up: a race only repeats it
+  if (ready.load(std::memory_order_acquire)) return cudaSuccess;
   // the setmaxnreg split (128 x 56 + 256 x 224) assumes 168 registers at launch
   cudaFuncAttributes fa{};
   cudaError_t e = cudaFuncGetAttributes(&fa, m4rm_scan_kernel<MR, NJ>);
@@ -449,7 +449,7 @@ cudaError_t m4_prepare() {
   e = cudaFuncSetAttribute(m4rm_scan_kernel<MR, NJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            M4Layout<MR>::kSmem);
   if (e != cudaSuccess) return e;
-  ready = true;
+  ready.store(true, std::memory_order_release);
   return cudaSuccess;
 }
 

@@ -16,6 +16,7 @@
 //                       one LOP3 (acc ^= mask & word) per request-word pair.
 //                       Items are (job, B-tile, W-tile, k-chunk), so the same
 //                       launch serves one table or many uneven tables.
+#include <atomic>
 #include <algorithm>
 
 #include "chacha.cuh"
@@ -759,43 +760,50 @@ cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st) {
 // host side
 // ---------------------------------------------------------------------------
 int device_sm_count() {
-  static int cached[64] = {0};
+  // per device, computed once (a race only repeats the query)
+  static std::atomic<int> cached[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return 1;
-  if (!cached[dev]) {
+  int c = cached[dev].load(std::memory_order_acquire);
+  if (!c) {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cached[dev] = v > 0 ? v : 1;
+    c = v > 0 ? v : 1;
+    cached[dev].store(c, std::memory_order_release);
   }
-  return cached[dev];
+  return c;
 }
 
 template <int NB>
 static int plain_occupancy() {
-  static int cached = 0;
-  if (!cached) {
+  static std::atomic<int> cached{0};  // computed once (a race only repeats the query)
+  int c = cached.load(std::memory_order_acquire);
+  if (!c) {
     int v = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, plain_scan_kernel<NB, 8>, 256, 0);
-    cached = v > 0 ? v : 1;
+    c = v > 0 ? v : 1;
+    cached.store(c, std::memory_order_release);
   }
-  return cached;
+  return c;
 }
 
 int plain_ctas_per_sm() { return plain_occupancy<1>(); }
 
 
 int batched_ctas_per_sm() {
-  static int cached = 0;
-  if (!cached) {
+  static std::atomic<int> cached{0};  // computed once (a race only repeats the query)
+  int c = cached.load(std::memory_order_acquire);
+  if (!c) {
     cudaFuncSetAttribute(batched_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kScanSmem);
     int v = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batched_scan_kernel, kScanThreads,
                                                   kScanSmem);
-    cached = v > 0 ? v : 1;
+    c = v > 0 ? v : 1;
+    cached.store(c, std::memory_order_release);
   }
-  return cached;
+  return c;
 }
 
 int scan_stage_bytes(const Shape& s) { return s.srows() * (s.wt() + s.bt()) * 4; }
@@ -849,8 +857,8 @@ bool finalize_job(ScanJob& j) {
 }
 
 cudaError_t launch_batched(const ScanLaunch& L, int grid, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<bool> attr_set{false};  // idempotent set-up: a race only repeats it
+  if (!attr_set.load(std::memory_order_acquire)) {
     // the setmaxnreg split is only safe with the register count it was sized for
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, batched_scan_kernel);
@@ -859,7 +867,7 @@ cudaError_t launch_batched(const ScanLaunch& L, int grid, cudaStream_t st) {
     e = cudaFuncSetAttribute(batched_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kScanSmem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true, std::memory_order_release);
   }
   if (L.total_items == 0) return cudaSuccess;
   return launch_pdl(batched_scan_kernel, dim3(grid), dim3(kScanThreads), kScanSmem, st, L);
@@ -874,12 +882,12 @@ cudaError_t launch_zero_outputs(const ScanLaunch& L, cudaStream_t st) {
 template <int NB, int CPT>
 static cudaError_t launch_plain_tma_t(const uint4* T4, uint64_t n, uint32_t U, const uint64_t* R,
                                       uint32_t words64, uint32_t B, uint4* o4, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<bool> attr_set{false};  // idempotent set-up: a race only repeats it
+  if (!attr_set.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(plain_tma_kernel<NB, CPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kPlainTmaSmem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true, std::memory_order_release);
   }
   uint64_t ctas = std::min<uint64_t>(device_sm_count(), n);
   const uint64_t rows_per_cta = (n + ctas - 1) / ctas;
@@ -956,15 +964,18 @@ cudaError_t launch_plain(const uint32_t* T, uint64_t n, uint32_t Wd, const uint6
 }
 
 int* device_status_word() {
-  static int* addr[64] = {nullptr};
+  // per device, looked up once (a race only repeats the lookup)
+  static std::atomic<int*> addr[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!addr[dev]) {
+  int* a = addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-    addr[dev] = static_cast<int*>(p);
+    a = static_cast<int*>(p);
+    addr[dev].store(a, std::memory_order_release);
   }
-  return addr[dev];
+  return a;
 }
 
 int read_device_status_and_clear(int* status) {
