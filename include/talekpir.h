@@ -159,11 +159,14 @@ tpir_status tpir_write_noalloc(tpir_db *db, uint64_t b1, uint64_t b2, const void
 tpir_status tpir_read_batch(tpir_db *db, const uint64_t *req_bits, uint32_t B, void *out);
 
 /* Synchronous, for request sets larger than one batch: B_total rows of
- * req_bits (host) in batches of `batch`, replies into out (host, B_total x
- * row_bytes).  Three device slots rotate: each batch's rows are copied in two
- * batches ahead of its scan and its replies copied out after it, on a copy
- * stream, so the copies overlap the scans (with pinned host buffers; pageable
- * ones work but serialise).  Same replies as tpir_read_batch on each batch. */
+ * req_bits (host) in batches of `batch` (one scan launch each), replies into
+ * out (host, B_total x row_bytes).  Three device slots rotate, each holding a
+ * group of four batches: a group's rows are copied in two groups ahead of
+ * its scans and its replies copied out after them, on a copy stream, so the
+ * copies overlap the scans (with pinned host buffers; pageable ones work but
+ * serialise), and the scans of a group run back to back.  Device memory for
+ * the slots is allocated on first use and kept with the db.  Same replies as
+ * tpir_read_batch on each batch. */
 tpir_status tpir_read_batch_pipelined(tpir_db *db, const uint64_t *req_bits, uint64_t B_total,
                                       uint32_t batch, void *out);
 

@@ -621,9 +621,17 @@ tpir_status tpir_read_batch_pipelined(tpir_db* db, const uint64_t* req_bits, uin
   if (!db) return TPIR_EINVAL;
   if (B_total == 0) return TPIR_OK;
   if (!req_bits || !out || batch == 0) return TPIR_EINVAL;
+  // Three device slots rotate, each holding a group of kGroup batches: the
+  // group's request rows are copied in two groups ahead of its scans and its
+  // replies copied out after them, on a copy stream.  The scans of a group
+  // follow one another with no stream operation between them, so each one's
+  // ramp-up overlaps the previous one's tail (programmatic dependent launch);
+  // only a group's first scan waits on the copy events.
   constexpr int kSlots = 3;
-  const uint64_t rb = static_cast<uint64_t>(batch) * db->words64 * 8;
-  const uint64_t ob = static_cast<uint64_t>(batch) * db->row_bytes;
+  constexpr uint64_t kGroup = 4;
+  const uint64_t gb = kGroup * batch;  // request rows per group
+  const uint64_t rb = gb * db->words64 * 8;
+  const uint64_t ob = gb * db->row_bytes;
   const uint64_t ra = (rb + 255) / 256 * 256, oa = (ob + 255) / 256 * 256;
   if (!grow_dev(reinterpret_cast<void**>(&db->d_pipe), &db->pipe_cap, kSlots * (ra + oa)))
     return TPIR_ENOMEM;
@@ -634,40 +642,44 @@ tpir_status tpir_read_batch_pipelined(tpir_db* db, const uint64_t* req_bits, uin
   if (e != cudaSuccess) return cuda_status(e);
   cudaStream_t cp = db->copy_stream, cs = db->stream;
   cudaEvent_t* in_done = db->pipe_ev;              // request rows copied in
-  cudaEvent_t* scan_done = db->pipe_ev + kSlots;   // scan of the slot done
+  cudaEvent_t* scan_done = db->pipe_ev + kSlots;   // scans of the slot done
   cudaEvent_t* out_done = db->pipe_ev + 2 * kSlots;  // replies copied out
-  const uint64_t nbatch = (B_total + batch - 1) / batch;
+  const uint64_t ngroup = (B_total + gb - 1) / gb;
   auto req_of = [&](uint64_t i) { return reinterpret_cast<uint64_t*>(db->d_pipe + (i % kSlots) * (ra + oa)); };
   auto out_of = [&](uint64_t i) { return db->d_pipe + (i % kSlots) * (ra + oa) + ra; };
-  auto rows = [&](uint64_t i) { return static_cast<uint32_t>(std::min<uint64_t>(batch, B_total - i * batch)); };
-  // copy-in of batch i: into its slot, once the scan that last read the slot is done
+  auto rows = [&](uint64_t i) { return std::min<uint64_t>(gb, B_total - i * gb); };
+  // copy-in of group i: into its slot, once the scans that last read the slot are done
   auto copy_in = [&](uint64_t i) -> cudaError_t {
     cudaError_t r = cudaSuccess;
     if (i >= kSlots) r = cudaStreamWaitEvent(cp, scan_done[i % kSlots], 0);
     if (r == cudaSuccess)
-      r = cudaMemcpyAsync(req_of(i), req_bits + i * batch * db->words64,
-                          static_cast<uint64_t>(rows(i)) * db->words64 * 8, cudaMemcpyHostToDevice, cp);
+      r = cudaMemcpyAsync(req_of(i), req_bits + i * gb * db->words64, rows(i) * db->words64 * 8,
+                          cudaMemcpyHostToDevice, cp);
     if (r == cudaSuccess) r = cudaEventRecord(in_done[i % kSlots], cp);
     return r;
   };
-  // copy-in runs two batches ahead, so it overlaps the scans; copy-out follows each scan
-  for (uint64_t i = 0; e == cudaSuccess && i < std::min<uint64_t>(2, nbatch); ++i) e = copy_in(i);
-  for (uint64_t i = 0; e == cudaSuccess && i < nbatch; ++i) {
+  for (uint64_t i = 0; e == cudaSuccess && i < std::min<uint64_t>(2, ngroup); ++i) e = copy_in(i);
+  for (uint64_t i = 0; e == cudaSuccess && i < ngroup; ++i) {
     const int s = static_cast<int>(i % kSlots);
     e = cudaStreamWaitEvent(cs, in_done[s], 0);
     if (e == cudaSuccess && i >= kSlots) e = cudaStreamWaitEvent(cs, out_done[s], 0);
     if (e != cudaSuccess) break;
-    const tpir_status st = enqueue_read(db, req_of(i), rows(i), out_of(i), cs);
-    if (st != TPIR_OK) {
-      cudaStreamSynchronize(cp);
-      return st;
+    for (uint64_t b0 = 0; b0 < rows(i); b0 += batch) {
+      const uint32_t nb = static_cast<uint32_t>(std::min<uint64_t>(batch, rows(i) - b0));
+      const tpir_status st = enqueue_read(db, req_of(i) + b0 * db->words64, nb,
+                                         out_of(i) + b0 * db->row_bytes, cs);
+      if (st != TPIR_OK) {
+        cudaStreamSynchronize(cp);
+        cudaStreamSynchronize(cs);
+        return st;
+      }
     }
     e = cudaEventRecord(scan_done[s], cs);
-    if (e == cudaSuccess && i + 2 < nbatch) e = copy_in(i + 2);
+    if (e == cudaSuccess && i + 2 < ngroup) e = copy_in(i + 2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cp, scan_done[s], 0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + i * batch * db->row_bytes, out_of(i),
-                          static_cast<uint64_t>(rows(i)) * db->row_bytes, cudaMemcpyDeviceToHost, cp);
+      e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + i * gb * db->row_bytes, out_of(i),
+                          rows(i) * db->row_bytes, cudaMemcpyDeviceToHost, cp);
     if (e == cudaSuccess) e = cudaEventRecord(out_done[s], cp);
   }
   const cudaError_t e2 = cudaStreamSynchronize(cp);
