@@ -158,11 +158,12 @@ def test_multi_table_one_launch_bit_exact():
 
 def test_multi_table_tensor_launch_chunks_and_request_paths():
     """More tables than one tensor-core launch holds (its parameters carry
-    two tensor maps per table, 64 tables per launch): 100 small tables of
-    >= 96 requests, forced to the tensor-core kernel, with even and odd
-    request-word counts and every third request block at an 8-byte offset
-    (per-thread loads instead of TMA staging), read in one call and from a
-    captured graph; every reply bit-exact."""
+    three tensor maps per table, 64 tables per launch): 100 small tables of
+    96..299 requests, forced to the tensor-core kernel, with even and odd
+    request-word counts (staged as rows and as row pairs) and every third
+    request block at an 8-byte offset (per-thread loads instead of TMA
+    staging), read in one call and from a captured graph; every reply
+    bit-exact."""
     torch = require_cuda()
     rng = np.random.default_rng(90)
     dbs, jobs, exp, keep = [], [], [], []
