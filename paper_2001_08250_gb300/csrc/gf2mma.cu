@@ -109,7 +109,6 @@ struct GJob {
   uint32_t Wd, words64, B;
   uint32_t n_strips, n_mb, kc_rows;
   uint32_t stages;       // stages (kGKStage buckets) per strip: ceil(n / kGKStage)
-  uint32_t span_w;       // span mode: stages per block (the order of the units)
   uint32_t item_begin;   // index of this job's first item in the launch
   uint32_t split;        // replies are initialised first and XOR-reduced into
   uint32_t req_tma;      // request words staged by TMA: 0 no, 1 rows, 2 row pairs
@@ -175,13 +174,11 @@ __device__ __forceinline__ uint32_t g_item_of(uint32_t r) {
 
 // This CTA's items in order.  Item mode: items c, ... of the launch list
 // (g_item_of).  Span mode (one job with at most about one k-chunk of stages
-// per CTA): the job's stages are ordered (M-block, block of span_w stages,
-// strip, stage) and cut into one contiguous span per CTA of equal length; an
-// item is a run of the span within one strip of one block and one k-chunk of
-// kGMaxCount buckets (chunks aligned to multiples of kGMaxCount).  With
-// span_w = all stages (strip-major) a CTA runs one or two items (accumulator
-// read-outs); with span_w about the span length the CTAs of one block read
-// the same rows, strip by strip, at about the same time.
+// per CTA): the job's stages are ordered (M-block, strip, stage) and cut into
+// one contiguous span per CTA of equal length; an item is a run of the span
+// within one strip and one k-chunk of kGMaxCount buckets (chunks aligned to
+// multiples of kGMaxCount), so a CTA runs one or two items (accumulator
+// read-outs).
 struct GWalk {
   uint64_t u, end;  // span mode: next stage unit, end of this CTA's span
   uint32_t r;       // item mode: next round
@@ -203,24 +200,11 @@ __device__ __forceinline__ bool g_walk_next(const GLaunch<NJ>& L, GWalk& w, GIte
     const uint64_t per_mb = static_cast<uint64_t>(J.n_strips) * J.stages;
     const uint64_t o = w.u % per_mb;
     const uint32_t mb = static_cast<uint32_t>(w.u / per_mb);
-    const uint64_t W = J.span_w, nfull = J.stages / W;
-    const uint64_t full_units = nfull * J.n_strips * W;
-    uint64_t bw, b0, r;  // block width, first stage, unit within the block
-    if (o < full_units) {
-      bw = W;
-      b0 = o / (J.n_strips * W) * W;
-      r = o % (J.n_strips * W);
-    } else {
-      bw = J.stages - nfull * W;
-      b0 = nfull * W;
-      r = o - full_units;
-    }
-    const uint64_t st = r % bw;  // stage within the block
-    const uint64_t kst = b0 + st;
+    const uint64_t kst = o % J.stages;  // stage within the strip
     constexpr uint64_t kChunk = kGMaxCount / kGKStage;  // stages per k-chunk
-    const uint64_t lim = min(w.end, min(w.u - st + bw, w.u - kst % kChunk + kChunk));
+    const uint64_t lim = min(w.end, min(w.u - kst + J.stages, w.u - kst % kChunk + kChunk));
     it.job = 0;
-    it.strip = static_cast<uint32_t>(r / bw);
+    it.strip = static_cast<uint32_t>(o / J.stages);
     it.k0 = kst * kGKStage;
     it.k1 = min(J.n, (kst + (lim - w.u)) * kGKStage);
     it.b0 = mb * 256u;
@@ -1003,16 +987,15 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
   const uint64_t grid = std::min<uint64_t>(units, device_sm_count());
   const uint64_t per_cta = (units + grid - 1) / grid;
   if (per_cta <= kGMaxCount / kGKStage) {
-    // span mode: equal runs of stages per CTA, strip-major (one block of
-    // all stages); partial strips of several CTAs XOR-reduce into replies
-    // initialised first.  Blocks of about one span (CTAs of a block reading
-    // the same rows together) cut DRAM reads of the paper-scale launch from
+    // span mode: equal runs of stages per CTA, strip-major; partial strips of
+    // several CTAs XOR-reduce into replies initialised first.  (Ordering the
+    // stages in blocks of about one span, so that the CTAs of a block read
+    // the same rows together, cut DRAM reads of the paper-scale launch from
     // 3x to 1.04x the table but took 7 % longer: the tail block's CTAs run
-    // several short items, and DRAM is not the bound here.
+    // several short items, and DRAM is not the bound here.)
     L.span = 1;
     L.units = units;
     J.kc_rows = static_cast<uint32_t>(kGMaxCount);
-    J.span_w = J.stages;
     J.split = 1;
     L.total_items = 0;
   } else {
