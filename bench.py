@@ -211,7 +211,7 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--legs", default="head,head_m4rm,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large,getupdates",
+    ap.add_argument("--legs", default="head,head_m4rm,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large,getupdates,writes",
                     help="comma list of: head (B=256, timed headline: the automatic choice, the "
                          "tensor-core kernel), head_m4rm / head_lop3 (B=256 on the Four-Russians / "
                          "register-tiled LOP3 kernel), plain (B=1), b32, masked (serialized-PIR "
@@ -480,6 +480,7 @@ def main() -> None:
                "sample": f"{sample} reads of the 128 MiB table (single-threaded C)"}
 
     getupdates = getupdates_leg(talekpir, synth, torch, stream) if ("getupdates" in args.legs and rank == 0) else None
+    writes = writes_leg(talekpir, synth) if ("writes" in args.legs and rank == 0) else None
 
     sweep = None
     if "serve_sweep" in args.legs and rank == 0:
@@ -518,6 +519,7 @@ def main() -> None:
             "multi_table": multi,
             "serve_sweep": sweep,
             "getupdates": getupdates,
+            "writes": writes,
             "large_table": large,
             "cpu_baseline": cpu,
         }
@@ -562,6 +564,57 @@ def getupdates_leg(talekpir, synth, torch, stream) -> dict:
     out["global_encode_us"] = ms * 1000
     db.close()
     return out
+
+
+def writes_leg(talekpir, synth) -> dict:
+    """Cuckoo writes (Section 5.3) and interest-vector updates (Section 7) on
+    the paper-scale table (n = 32768 x 4 x 1 KiB), collection capacity 95 % of
+    the slots (the load of the paper's cost table), at most 500 evictions: the
+    table is first filled to 90 %, then 4096 writes are timed in batches of
+    256 (tpir_write_batch: host placement, then the slot moves and payloads on
+    the device) and 256 more one by one (tpir_write); interest vectors of
+    m = 2^20 bits, k = 4, 65 536 writes' positions per call.  The calls are
+    synchronous: host wall-clock."""
+    n, d, z = N_BUCKETS, D_SLOTS, MSG_BYTES
+    cap = int(0.95 * n * d)
+    fill = int(0.90 * n * d)
+    timed_batch, timed_single, per = 4096, 256, 256
+    db = talekpir.DB(n, d, z)
+    db.set_policy(cap, 500, 11)
+    keys = synth.write_keys(fill + timed_batch + timed_single, seed=12)
+    b1, b2 = synth.bucket_pairs(keys, n)
+    M = synth.messages(4096, z, seed=12)  # payload bytes do not change the cost
+    for i in range(0, fill, 4096):
+        j = min(fill, i + 4096)
+        db.write_batch(b1[i:j], b2[i:j], M[: j - i])
+    ev_total, efull = 0, 0
+    t0 = time.perf_counter()
+    for i in range(fill, fill + timed_batch, per):
+        st, ev = db.write_batch(b1[i:i + per], b2[i:i + per], M[:per])
+        ev_total += int(ev.sum())
+        efull += int((st != talekpir.OK).sum())
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for i in range(fill + timed_batch, fill + timed_batch + timed_single):
+        rc, ev = db.write(int(b1[i]), int(b2[i]), M[i % 4096])
+        ev_total += ev
+        efull += int(rc != talekpir.OK)
+    ts = time.perf_counter() - t0
+    db.bloom_create(1 << 20, 4, 1, 0)
+    pos = synth.bloom_positions(keys[:65536], 1 << 20, 4)
+    assert db.bloom_insert_batch(pos) == talekpir.OK
+    t0 = time.perf_counter()
+    for _ in range(10):
+        assert db.bloom_insert_batch(pos) == talekpir.OK
+    tbl = (time.perf_counter() - t0) / 10
+    db.close()
+    return {"table": "n=32768 x 4 x 1024 B, capacity 95 % of slots, filled to 90 %",
+            "batched_writes_per_s": timed_batch / tb, "batch": per,
+            "batched_us_per_write": tb / timed_batch * 1e6,
+            "single_write_us": ts / timed_single * 1e6,
+            "mean_evictions": ev_total / (timed_batch + timed_single), "efull": efull,
+            "interest_vector_updates_per_s": 65536 / tbl, "interest_vector_m_bits": 1 << 20,
+            "interest_vector_k": 4}
 
 
 def sharded_leg(talekpir, torch, stream, T, dR, args, legs) -> dict:
