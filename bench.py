@@ -470,14 +470,7 @@ def main() -> None:
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
     cpu = None
     if rank == 0 and "cpu" in args.legs:
-        import oracle
-        oracle.build()
-        sample = 8
-        t0 = time.perf_counter()
-        oracle.read_batch(T, n, d, z, R[:sample])
-        cdt = time.perf_counter() - t0
-        cpu = {"value": sample / cdt, "unit": "reads/s", "cores": 1, "kind": "oracle",
-               "sample": f"{sample} reads of the 128 MiB table (single-threaded C)"}
+        cpu = cpu_leg(T, R)
 
     getupdates = getupdates_leg(talekpir, synth, torch, stream) if ("getupdates" in args.legs and rank == 0) else None
     writes = writes_leg(talekpir, synth) if ("writes" in args.legs and rank == 0) else None
@@ -531,6 +524,36 @@ def main() -> None:
 
 
 SHARDS = 4
+
+
+def cpu_leg(T, R) -> dict:
+    """CPU baselines on this host, reported only: the oracle (single-threaded
+    C, one pass over the table per read) on 8 reads, and the paper-style
+    multi-core engine (Section 9.2's CPU server: one pass over the table per
+    batch, buckets split over pthreads on every core) on batches of B_HEAD
+    reads of the same table."""
+    import oracle
+    n, d, z = N_BUCKETS, D_SLOTS, MSG_BYTES
+    oracle.build()
+    oracle.build_engine()
+    nproc = os.cpu_count() or 1
+    sample = 8
+    t0 = time.perf_counter()
+    oracle.read_batch(T, n, d, z, R[:sample])
+    cdt = time.perf_counter() - t0
+    oracle.engine_read_batch(T, n, d, z, R[:B_HEAD], threads=nproc)   # pages in, warms up
+    reps = 3
+    t0 = time.perf_counter()
+    for r in range(reps):
+        oracle.engine_read_batch(T, n, d, z, R[(r + 1) * B_HEAD:(r + 2) * B_HEAD], threads=nproc)
+    edt = (time.perf_counter() - t0) / reps
+    return {"value": sample / cdt, "unit": "reads/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample} reads of the 128 MiB table (single-threaded C)",
+            "host_cores": nproc,
+            "multi_core": {"value": B_HEAD / edt, "unit": "reads/s", "cores": nproc,
+                           "threads": nproc,
+                           "kind": "paper-style batched CPU scan (pthreads, one table pass per batch)",
+                           "sample": f"{reps} batches of {B_HEAD} reads of the 128 MiB table"}}
 
 
 def getupdates_leg(talekpir, synth, torch, stream) -> dict:

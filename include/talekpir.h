@@ -122,7 +122,11 @@ tpir_status tpir_db_dump(tpir_db *db, void *host_table, size_t bytes);
  * the db's stream order, after every read submitted before this call and
  * before every read submitted after it.  Returns EFULL (nothing changed; the
  * random draws stay consumed) when the walk exceeds max_evictions.
- * *evictions_out (may be NULL) = evictions made. */
+ * *evictions_out (may be NULL) = evictions made.  The move list and the
+ * message travel in the launch itself when they are small (up to 384 moves
+ * and 20 KiB of messages), so such a write returns as soon as it is
+ * enqueued; larger ones go through a staging buffer kept with the db.  On a
+ * CUDA or allocation failure the placement is taken back. */
 tpir_status tpir_write(tpir_db *db, uint64_t b1, uint64_t b2, const void *msg,
                        uint32_t *evictions_out);
 
@@ -145,11 +149,16 @@ tpir_status tpir_write_batch(tpir_db *db, uint32_t count, const uint64_t *b1, co
  * after every read already submitted on this db and before every later read.
  * Limits: msg_bytes <= 65536 and the db's max_evictions <= 500, else
  * TPIR_EINVAL (nothing changes).  EFULL as for tpir_write.
+ * The moves run after every earlier write to this db, on whatever stream it
+ * ran.  On any error the placement is taken back (table and metadata
+ * unchanged).  Not allowed while `stream` is being captured into a graph
+ * (TPIR_EINVAL): the events that order it against the db's other work
+ * cannot cross a capture boundary.
  * The moves use one temporary slot held in a 64 KiB device array that every
- * GPU loading the library keeps until exit.  The first call on a device looks
- * up that array's address, so make it before any stream capture.  All calls
- * share the array: calls whose moves overlap on the GPU (writes to different
- * dbs on different streams) race, so order them on one stream. */
+ * GPU loading the library keeps until exit; the first call on a device looks
+ * up that array's address.  All calls share the array: calls whose moves
+ * overlap on the GPU (writes to different dbs on different streams) race, so
+ * order them on one stream. */
 tpir_status tpir_write_noalloc(tpir_db *db, uint64_t b1, uint64_t b2, const void *d_msg,
                                uint32_t *evictions_out, void *stream);
 

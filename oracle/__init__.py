@@ -273,3 +273,41 @@ class Bloom:
     def contains(self, positions) -> bool:
         p = np.ascontiguousarray(positions, dtype=np.uint64)
         return bool(lib().oracle_bloom_contains(self.h, _ptr(p)))
+
+
+# ---- the paper-style multi-core CPU engine (a reported baseline, not an oracle)
+
+ENGINE_PATH = os.path.join(HERE, "libcpuengine.so")
+_engine = None
+
+
+def build_engine(force: bool = False) -> str:
+    """Compile cpu_engine.c into libcpuengine.so (gcc -O3, pthreads; portable
+    code: no machine-specific flags)."""
+    src = os.path.join(HERE, "cpu_engine.c")
+    if force or not os.path.exists(ENGINE_PATH) or os.path.getmtime(ENGINE_PATH) < os.path.getmtime(src):
+        tmp = ENGINE_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O3", "-fPIC", "-shared", "-pthread", "-o", tmp,
+                               src])
+        os.replace(tmp, ENGINE_PATH)
+    return ENGINE_PATH
+
+
+def engine_read_batch(T: np.ndarray, n: int, d: int, z: int, R: np.ndarray,
+                      threads: int | None = None) -> np.ndarray:
+    """Replies to the B request rows of R from the multi-core CPU engine."""
+    global _engine
+    if _engine is None:
+        L = ctypes.CDLL(build_engine())
+        L.cpu_engine_read_batch.argtypes = [_vp, _u64, _u64, _vp, _u32, _vp, _u32]
+        L.cpu_engine_read_batch.restype = ctypes.c_int
+        _engine = L
+    T = np.ascontiguousarray(T, dtype=np.uint8)
+    R = np.ascontiguousarray(R, dtype=np.uint64)
+    B = R.shape[0]
+    out = np.empty((B, d * z), dtype=np.uint8)
+    th = threads or os.cpu_count() or 1
+    rc = _engine.cpu_engine_read_batch(_ptr(T), n, d * z, _ptr(R), B, _ptr(out), th)
+    if rc != 0:
+        raise RuntimeError("cpu engine failed")
+    return out

@@ -66,9 +66,10 @@ int64_t CuckooMeta::lowest_free(uint64_t e) const {
 }
 
 tpir_status CuckooMeta::insert(uint64_t b1, uint64_t b2, uint64_t payload_idx,
-                               std::vector<MoveOp>& ops, uint32_t* evictions) {
+                               std::vector<MoveOp>& ops, uint32_t* evictions, Undo* undo) {
   if (evictions) *evictions = 0;
   if (b1 >= n_ || b2 >= n_) return TPIR_EINVAL;
+  const uint64_t rng0 = rng_;
 
   // undo logs: (slot, previous item) and (item seq, previous slot)
   std::vector<std::pair<uint64_t, uint64_t>> undo_slot, undo_item;
@@ -135,6 +136,15 @@ tpir_status CuckooMeta::insert(uint64_t b1, uint64_t b2, uint64_t payload_idx,
   }
 
   // commit the new item
+  if (undo) {
+    undo->head = old_head;
+    undo->live = old_live;
+    undo->next_seq = next_seq_;
+    undo->rng = rng0;
+    undo->ring_b1 = item_b1_[next_seq_ % ring_];
+    undo->ring_b2 = item_b2_[next_seq_ % ring_];
+    undo->ring_slot = item_slot_[next_seq_ % ring_];
+  }
   const uint64_t seq = next_seq_++;
   item_b1_[seq % ring_] = b1;
   item_b2_[seq % ring_] = b2;
@@ -189,7 +199,27 @@ tpir_status CuckooMeta::insert(uint64_t b1, uint64_t b2, uint64_t payload_idx,
   }
   ops.push_back(MoveOp{new_slot, payload_idx, 1u, 0u});
   (void)gc_slot;
+  if (undo) {
+    undo->slots = std::move(undo_slot);
+    undo->items = std::move(undo_item);
+  }
   return TPIR_OK;
+}
+
+void CuckooMeta::rollback(const Undo& u) {
+  // the new item's ring entry, then positions and slots in reverse order
+  // (the slot log restores the new item's slot too: it was logged when the
+  // item was placed)
+  const uint64_t r = u.next_seq % ring_;
+  item_b1_[r] = u.ring_b1;
+  item_b2_[r] = u.ring_b2;
+  item_slot_[r] = u.ring_slot;
+  for (auto it = u.items.rbegin(); it != u.items.rend(); ++it) islot(it->first) = it->second;
+  for (auto it = u.slots.rbegin(); it != u.slots.rend(); ++it) slot_item_[it->first] = it->second;
+  head_ = u.head;
+  live_ = u.live;
+  next_seq_ = u.next_seq;
+  rng_ = u.rng;
 }
 
 }  // namespace tpir

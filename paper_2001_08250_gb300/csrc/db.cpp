@@ -204,32 +204,66 @@ tpir_status apply_writes_core(tpir_db* db, uint32_t count, const uint64_t* b1, c
   std::vector<MoveOp> ops;
   ops.reserve(count * 2);
   const uint64_t z = db->z;
+  // every successful insert is recorded so that the whole call can be taken
+  // back if its device work cannot be enqueued: then nothing has changed,
+  // not even the random draws of eviction walks that failed with EFULL
+  std::vector<CuckooMeta::Undo> undos;
+  undos.reserve(count);
+  std::vector<tpir_status> sts(count);
+  std::vector<uint32_t> evs(count);
+  const uint64_t rng0 = db->meta->rng_state();
   uint32_t ok = 0;
   for (uint32_t i = 0; i < count; ++i) {
-    uint32_t ev = 0;
-    const tpir_status s = db->meta->insert(b1[i], b2[i], i, ops, &ev);
-    if (st_out) st_out[i] = s;
-    if (ev_out) ev_out[i] = ev;
-    if (s == TPIR_OK) ++ok;
+    CuckooMeta::Undo u;
+    sts[i] = db->meta->insert(b1[i], b2[i], i, ops, &evs[i], &u);
+    if (sts[i] == TPIR_OK) {
+      ++ok;
+      undos.push_back(std::move(u));
+    }
   }
+  auto take_back = [&]() {
+    for (auto it = undos.rbegin(); it != undos.rend(); ++it) db->meta->rollback(*it);
+    db->meta->set_rng_state(rng0);
+  };
   if (!ops.empty()) {
     const uint64_t pay_bytes = count * z;
-    const uint64_t ops_bytes = ops.size() * sizeof(MoveOp);
-    if (!grow_pinned(reinterpret_cast<void**>(&stg.h), &stg.h_cap, pay_bytes + ops_bytes) ||
-        !grow_dev(reinterpret_cast<void**>(&stg.d_payload), &stg.pay_cap, pay_bytes) ||
-        !grow_dev(reinterpret_cast<void**>(&stg.d_ops), &stg.ops_cap, ops_bytes))
-      return TPIR_ENOMEM;
-    std::memcpy(stg.h, msgs, pay_bytes);
-    std::memcpy(stg.h + pay_bytes, ops.data(), ops_bytes);
-    cudaError_t e = cudaMemcpyAsync(stg.d_payload, stg.h, pay_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(stg.d_ops, stg.h + pay_bytes, ops_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = launch_apply_moves(db->d_table, db->z, stg.d_ops, static_cast<uint32_t>(ops.size()),
-                             stg.d_payload, db->d_tmp, st);
+    cudaError_t e = cudaSuccess;
+    if (ops.size() <= kParamOps && pay_bytes <= kParamBytes) {
+      // small batch (a single write): moves and messages by value in the
+      // kernel parameters, one launch, no staging to wait for
+      thread_local ParamMoves m;
+      m.nops = static_cast<uint32_t>(ops.size());
+      m.pad = 0;
+      std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
+      std::memcpy(m.payload, msgs, pay_bytes);
+      e = launch_apply_moves_param(db->d_table, db->z, m, db->d_tmp, st);
+    } else {
+      const uint64_t ops_bytes = ops.size() * sizeof(MoveOp);
+      if (!grow_pinned(reinterpret_cast<void**>(&stg.h), &stg.h_cap, pay_bytes + ops_bytes) ||
+          !grow_dev(reinterpret_cast<void**>(&stg.d_payload), &stg.pay_cap, pay_bytes) ||
+          !grow_dev(reinterpret_cast<void**>(&stg.d_ops), &stg.ops_cap, ops_bytes) ||
+          (!stg.done && cudaEventCreateWithFlags(&stg.done, cudaEventDisableTiming) != cudaSuccess)) {
+        take_back();
+        return TPIR_ENOMEM;
+      }
+      std::memcpy(stg.h, msgs, pay_bytes);
+      std::memcpy(stg.h + pay_bytes, ops.data(), ops_bytes);
+      e = cudaMemcpyAsync(stg.d_payload, stg.h, pay_bytes, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(stg.d_ops, stg.h + pay_bytes, ops_bytes, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = launch_apply_moves(db->d_table, db->z, stg.d_ops, static_cast<uint32_t>(ops.size()),
+                               stg.d_payload, db->d_tmp, st);
+      if (e == cudaSuccess) e = cudaEventRecord(stg.done, st);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) {
+      take_back();
+      return cuda_status(e);
+    }
   }
+  if (st_out) std::copy(sts.begin(), sts.end(), st_out);
+  if (ev_out) std::copy(evs.begin(), evs.end(), ev_out);
   db->epoch += ok;
   return TPIR_OK;
 }
@@ -244,7 +278,8 @@ tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, 
     if (pos[i] >= bl.m) return TPIR_EINVAL;
   const uint64_t bytes = static_cast<uint64_t>(count) * bl.k * 8;
   if (!grow_pinned(reinterpret_cast<void**>(&stg.h), &stg.h_cap, bytes) ||
-      !grow_dev(reinterpret_cast<void**>(&stg.d_pos), &stg.pos_cap, bytes))
+      !grow_dev(reinterpret_cast<void**>(&stg.d_pos), &stg.pos_cap, bytes) ||
+      (!stg.done && cudaEventCreateWithFlags(&stg.done, cudaEventDisableTiming) != cudaSuccess))
     return TPIR_ENOMEM;
   std::memcpy(stg.h, pos, bytes);
   cudaError_t e = cudaMemcpyAsync(stg.d_pos, stg.h, bytes, cudaMemcpyHostToDevice, st);
@@ -265,6 +300,7 @@ tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, 
     bl.count += seg;
     i += seg;
   }
+  if (e == cudaSuccess) e = cudaEventRecord(stg.done, st);
   if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
   return cuda_status(e);
 }
@@ -367,6 +403,7 @@ void tpir_write_staging_release(tpir_write_staging& s) {
   cudaFree(s.d_payload);
   cudaFree(s.d_ops);
   cudaFree(s.d_pos);
+  if (s.done) cudaEventDestroy(s.done);
   s = tpir_write_staging();
 }
 
@@ -578,9 +615,12 @@ tpir_status tpir_write_batch(tpir_db* db, uint32_t count, const uint64_t* b1, co
   if (!db || (count && (!b1 || !b2 || !msgs))) return TPIR_EINVAL;
   if (db->n_total) return TPIR_EINVAL;  // shards hold snapshots: no cuckoo writes
   if (count == 0) return TPIR_OK;
-  // the staging of the previous call must have been consumed
-  cudaError_t e = cudaEventSynchronize(db->last_write);
-  if (e != cudaSuccess) return cuda_status(e);
+  // the staging of the previous call that used it must have been consumed
+  // (small batches pass their moves in the kernel parameters and use none)
+  if (db->stage.done) {
+    cudaError_t e = cudaEventSynchronize(db->stage.done);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   order_writes_after_reads(db, db->stream);
   return apply_writes_core(db, count, b1, b2, static_cast<const uint8_t*>(msgs), status_out,
                            evictions_out, db->stream, db->stage);

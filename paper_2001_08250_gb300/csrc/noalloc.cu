@@ -84,26 +84,39 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
   if (db->z > kNoallocMaxMsgBytes) return TPIR_EINVAL;                   // slot too large
   if (db->meta->max_evictions() > kNoallocMaxEvictions) return TPIR_EINVAL;
   if (b1 >= db->n || b2 >= db->n) return TPIR_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the events that order this write against the db's other work cannot be
+  // used across a capture boundary: refuse a stream being captured
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return TPIR_ECUDA;
+  if (cap != cudaStreamCaptureStatusNone) return TPIR_EINVAL;
   void* tmp = nullptr;
   tpir_status s = noalloc_scratch(&tmp);
   if (s != TPIR_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   std::vector<MoveOp> ops;
   uint32_t ev = 0;
-  s = db->meta->insert(b1, b2, 0, ops, &ev);
-  if (evictions_out) *evictions_out = ev;
-  if (s != TPIR_OK) return s;  // EFULL: metadata rolled back, nothing to move
-  if (ops.size() > kNoallocMaxOps) return TPIR_EINVAL;  // cannot happen within the bounds above
+  CuckooMeta::Undo undo;
+  s = db->meta->insert(b1, b2, 0, ops, &ev, &undo);
+  if (s != TPIR_OK) {  // EFULL: metadata rolled back, nothing to move
+    if (evictions_out) *evictions_out = ev;
+    return s;
+  }
+  if (ops.size() > kNoallocMaxOps) {  // cannot happen within the bounds above
+    db->meta->rollback(undo);
+    return TPIR_EINVAL;
+  }
   NoallocMoves m;
   m.count = static_cast<uint32_t>(ops.size());
   m.pad = 0;
   std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
 
   // after every read already submitted on this db (its own stream included)
+  // and after every earlier write to it, whichever stream that ran on
   order_writes_after_reads(db, st);
   cudaError_t e = cudaEventRecord(db->stream_mark, db->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, db->stream_mark, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, db->last_write, 0);
   if (e == cudaSuccess) {
     apply_moves_noalloc_kernel<<<1, 256, 0, st>>>(db->d_table, db->z, m,
                                                   static_cast<const uint8_t*>(d_msg),
@@ -111,7 +124,12 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
-  if (e != cudaSuccess) return cuda_status(e);
+  if (e != cudaSuccess) {
+    // the host placement is taken back: the table and its metadata agree
+    db->meta->rollback(undo);
+    return cuda_status(e);
+  }
+  if (evictions_out) *evictions_out = ev;
   db->epoch += 1;
   return TPIR_OK;
 }

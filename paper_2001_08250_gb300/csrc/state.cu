@@ -34,6 +34,30 @@ __global__ void __launch_bounds__(256) apply_moves_kernel(uint8_t* __restrict__ 
   }
 }
 
+// The same moves for a small batch of writes, with the move list and the new
+// messages passed by value in the kernel parameters: no staging buffer, no
+// copy before the launch, so a single write costs one launch.
+__global__ void __launch_bounds__(256) apply_moves_param_kernel(uint8_t* __restrict__ table,
+                                                                uint32_t z,
+                                                                const __grid_constant__ ParamMoves m,
+                                                                uint8_t* __restrict__ tmp) {
+  const uint32_t z4 = z / 16;
+  for (uint32_t i = 0; i < m.nops; ++i) {
+    const MoveOp op = m.ops[i];
+    uint4* dst = reinterpret_cast<uint4*>(op.dst == kTmpSlot ? tmp : table + op.dst * z);
+    if (op.kind == 2) {
+      for (uint32_t j = threadIdx.x; j < z4; j += blockDim.x) dst[j] = make_uint4(0u, 0u, 0u, 0u);
+    } else if (op.kind == 1) {
+      const uint4* src = reinterpret_cast<const uint4*>(m.payload + op.src * z);
+      for (uint32_t j = threadIdx.x; j < z4; j += blockDim.x) dst[j] = src[j];
+    } else {
+      const uint4* src = reinterpret_cast<const uint4*>(op.src == kTmpSlot ? tmp : table + op.src * z);
+      for (uint32_t j = threadIdx.x; j < z4; j += blockDim.x) dst[j] = src[j];
+    }
+    __syncthreads();  // the next op may read what this one wrote
+  }
+}
+
 __global__ void bloom_set_kernel(uint64_t* __restrict__ delta, const uint64_t* __restrict__ pos,
                                  uint64_t count) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
@@ -70,6 +94,13 @@ cudaError_t launch_apply_moves(uint8_t* table, uint32_t z, const MoveOp* ops, ui
                                const uint8_t* payloads, uint8_t* tmp, cudaStream_t st) {
   if (nops == 0) return cudaSuccess;
   apply_moves_kernel<<<1, 256, 0, st>>>(table, z, ops, nops, payloads, tmp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMoves& m, uint8_t* tmp,
+                                     cudaStream_t st) {
+  if (m.nops == 0) return cudaSuccess;
+  apply_moves_param_kernel<<<1, 256, 0, st>>>(table, z, m, tmp);
   return cudaGetLastError();
 }
 

@@ -142,6 +142,20 @@ struct MoveOp {   // one step of a write's slot moves, executed in order
 constexpr uint64_t kTmpSlot = ~0ull;
 cudaError_t launch_apply_moves(uint8_t* table, uint32_t z, const MoveOp* ops, uint32_t nops,
                                const uint8_t* payloads, uint8_t* tmp, cudaStream_t st);
+// A small batch of writes with its moves and new messages in the kernel
+// parameters (no staging): at most kParamOps moves and kParamBytes of
+// messages (payload index i = bytes i*z .. of `payload`).
+constexpr uint32_t kParamOps = 384;
+constexpr uint32_t kParamBytes = 20 * 1024;
+struct ParamMoves {
+  uint32_t nops;
+  uint32_t pad;
+  MoveOp ops[kParamOps];
+  __align__(16) uint8_t payload[kParamBytes];
+};
+static_assert(sizeof(ParamMoves) + 64 < 32000, "kernel parameters must stay below 32 KB");
+cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMoves& m, uint8_t* tmp,
+                                     cudaStream_t st);
 cudaError_t launch_bloom_set(uint64_t* delta, const uint64_t* pos, uint64_t count, cudaStream_t st);
 cudaError_t launch_bloom_or(uint64_t* delta, const uint64_t* vec, uint64_t m, cudaStream_t st);
 cudaError_t launch_bloom_union(const uint64_t* deltas, uint32_t window, uint64_t words,
@@ -199,12 +213,27 @@ class CuckooMeta {
   void set_policy(uint64_t capacity, uint32_t max_evictions, uint64_t seed);
   void clear();
   uint64_t live() const { return live_; }
+  // What one successful insert changed, so that a caller whose device work
+  // could not be enqueued can take it back (rollback): the slots and item
+  // positions it overwrote, the ring entry of the new item, and the counters
+  // and generator state before it.
+  struct Undo {
+    std::vector<std::pair<uint64_t, uint64_t>> slots, items;
+    uint64_t head = 0, live = 0, next_seq = 0, rng = 0;
+    uint64_t ring_b1 = 0, ring_b2 = 0, ring_slot = 0;
+  };
   // Returns TPIR_OK / TPIR_EINVAL / TPIR_EFULL; on OK appends the moves to
-  // `ops` (payload index `payload_idx` for the new message).
+  // `ops` (payload index `payload_idx` for the new message) and, if `undo`
+  // is given, records how to take the insert back.
   tpir_status insert(uint64_t b1, uint64_t b2, uint64_t payload_idx, std::vector<MoveOp>& ops,
-                     uint32_t* evictions);
+                     uint32_t* evictions, Undo* undo = nullptr);
+  // Takes back a successful insert (the most recent one not yet taken back):
+  // the metadata, counters and generator are as if it had not been made.
+  void rollback(const Undo& u);
   uint64_t capacity() const { return capacity_; }
   uint32_t max_evictions() const { return max_ev_; }
+  uint64_t rng_state() const { return rng_; }
+  void set_rng_state(uint64_t r) { rng_ = r; }
 
  private:
   static constexpr uint64_t kEmpty = ~0ull;
@@ -236,6 +265,7 @@ struct tpir_write_staging {
   uint64_t ops_cap = 0;
   uint64_t* d_pos = nullptr;
   uint64_t pos_cap = 0;
+  cudaEvent_t done = nullptr;  // recorded after the last work that read the staging
   void release();
 };
 

@@ -95,6 +95,46 @@ def stream(key: int, count: int, start: int = 0) -> np.ndarray:
     return mix64(idx)
 
 
+def _signed(x: int) -> int:
+    x &= M64
+    return x - (1 << 64) if x >> 63 else x
+
+
+def stream_torch(key: int, count: int, start: int = 0, device="cuda"):
+    """The same outputs as ``stream`` computed with torch int64 tensors on
+    ``device`` (two's-complement wrapping arithmetic; logical right shifts
+    done as arithmetic shifts masked to the low bits), for inputs too large
+    to generate quickly on the host.  Returns an int64 tensor holding the
+    uint64 bit patterns."""
+    import torch
+    idx = torch.arange(start + 1, start + count + 1, dtype=torch.int64, device=device)
+    z = idx * _signed(GAMMA) + _signed(key)
+
+    def shr(x, s):
+        return (x >> s) & ((1 << (64 - s)) - 1)
+
+    z = (z ^ shr(z, 30)) * _signed(_C1)
+    z = (z ^ shr(z, 27)) * _signed(_C2)
+    return z ^ shr(z, 31)
+
+
+def table_bytes_torch(n: int, d: int, msg_bytes: int, seed: int = 0, table: int = 0,
+                      device="cuda"):
+    """``table_bytes`` generated on ``device``: a uint8 tensor [n, d*msg_bytes]
+    with the same bytes."""
+    import torch
+    W = d * msg_bytes
+    assert W % 8 == 0
+    total = n * W // 8
+    out = torch.empty(total, dtype=torch.int64, device=device)
+    key = stream_key(seed, table, P_TABLE)
+    chunk = 1 << 26
+    for s0 in range(0, total, chunk):
+        c = min(chunk, total - s0)
+        out[s0:s0 + c] = stream_torch(key, c, s0, device)
+    return out.view(torch.uint8).view(n, W)
+
+
 def words_per_row(n: int) -> int:
     """u64 words in one packed request row of ``n`` bits (LSB-first)."""
     return (n + 63) // 64

@@ -1,9 +1,9 @@
-// Throughput probe behind two design decisions of the read kernels:
+// Throughput measurement behind two design decisions of the read kernels
+// (compiled and run by tests/test_gpu_alu_rates.py):
 //  - the integer roofline of the batched read: how many LOP3 (acc = (a & b) ^ acc,
 //    the conditional-XOR of one 32-bit word) an SM retires per clock;
 //  - whether the 1-bit AND-POPC form of the GF(2) product can beat it: the
 //    throughput of mma.sync.aligned.m16n8k256 b1 and.popc on this part.
-// Build and run:  nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o alu_peak alu_peak.cu && ./alu_peak
 #include <cstdio>
 #include <cstdint>
 #include <cuda_runtime.h>
