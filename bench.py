@@ -9,9 +9,11 @@ so every pass streams its table from HBM.
 
 Reported: reads/s of the step (`value`), per-batch-width legs (B = 1 plain
 kernel, 32, 256) with their table-scan GB/s, the end-to-end rate through the
-synchronous host-buffer entry point (`e2e`), the oracle timed on the host
-(`cpu_baseline`), a short continuous-batching serve run (p50/p99), SM clocks
-sampled during the timed region, and the roofline of the dominant kernel.
+synchronous host-buffer entry point (`e2e`), the oracle and a multi-core CPU
+engine timed on the host (`cpu_baseline`), the 64-table uneven workload, the
+4 GiB table, writes, serving under a 64 GiB budget at Poisson 5 k and 50 k
+reads/s (p50/p99), SM clocks sampled during the timed region, and the
+roofline of the dominant kernel.
 
 Multi-GPU: every rank serves its own 32000 reads from its own replica of the
 table (the paper's servers each hold a full copy); no data-path collective,
@@ -211,23 +213,24 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--legs", default="head,head_m4rm,head_lop3,plain,b32,masked,sharded,e2e,serve,cpu,multi,large,getupdates,writes",
+    ap.add_argument("--legs", default="head,head_m4rm,head_lop3,plain,b32,masked,sharded,e2e,serve_sweep,cpu,multi,large,getupdates,writes",
                     help="comma list of: head (B=256, timed headline: the automatic choice, the "
                          "tensor-core kernel), head_m4rm / head_lop3 (B=256 on the Four-Russians / "
                          "register-tiled LOP3 kernel), plain (B=1), b32, masked (serialized-PIR "
                          "masked replies at B=256 and B=1), sharded (the table in 4 row shards "
                          "on this GPU, partial replies XOR-combined), getupdates (compressed "
                          "interest-vector deltas), "
-                         "e2e (host buffers), serve, cpu (oracle baseline), multi (64 uneven "
-                         "tables, one graph-captured launch), large (4 GiB table, B=1024); "
-                         "serve_sweep (not default: tables filling a 64 GiB budget, Poisson "
-                         "arrivals at --sweep-rates)")
+                         "e2e (host buffers), cpu (oracle and multi-core CPU baselines), multi "
+                         "(64 uneven tables, one graph-captured launch), large (4 GiB table, "
+                         "B=1024), writes, serve_sweep (tables filling a 64 GiB budget, Poisson "
+                         "arrivals at --sweep-rates for --sweep-seconds each); serve (not "
+                         "default: a short run on eight tables at --serve-rate)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the tile-shape autotuner (use the built-in shape choice)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
-    ap.add_argument("--sweep-rates", default="5000,10000,20000,50000",
+    ap.add_argument("--sweep-rates", default="5000,50000",
                     help="read arrival rates of the serve_sweep leg")
-    ap.add_argument("--sweep-seconds", type=float, default=6.0)
+    ap.add_argument("--sweep-seconds", type=float, default=10.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -479,7 +482,7 @@ def main() -> None:
     if "serve_sweep" in args.legs and rank == 0:
         sweep = serve_sweep_leg(talekpir, synth, torch, stream, args)
     multi = multi_leg(talekpir, synth, torch, stream, args) if "multi" in args.legs else None
-    large = large_leg(talekpir, torch, stream, args, hbm_peak) if "large" in args.legs else None
+    large = large_leg(talekpir, synth, torch, stream, args, hbm_peak) if "large" in args.legs else None
 
     gpu_launches = args.steps * ((USERS + B_HEAD - 1) // B_HEAD) * 2  # zero + scan per batch
     if rank == 0:
@@ -685,14 +688,6 @@ def sharded_leg(talekpir, torch, stream, T, dR, args, legs) -> dict:
             "overhead_vs_unsharded": (ms / base - 1.0) if base else None}
 
 
-def _fill_random(db, nbytes, gen, torch, stream):
-    """Uniform random payload generated on the device (seeded), loaded in place."""
-    t = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device="cuda", generator=gen)
-    db.load_async(t, stream)
-    torch.cuda.synchronize()
-    del t
-
-
 def _events_ms(torch, stream, fn, reps):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -710,14 +705,15 @@ def multi_leg(talekpir, synth, torch, stream, args) -> dict:
     the tensor-core kernel for the rest, one launch per request-staging
     mode), against 64 separate launches each taking the automatic choice."""
     shapes = synth.multi_table_shapes(64, seed=3)
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(3)
     jobs, dbs, total_bytes, reads, ops = [], [], 0, 0, 0
-    for (n, d, z, B) in shapes:
+    for i, (n, d, z, B) in enumerate(shapes):
+        # the same seeded inputs as the parity test of this workload
         db = talekpir.DB(n, d, z)
-        _fill_random(db, n * d * z, gen, torch, stream)
-        R = torch.randint(-(1 << 63), (1 << 63) - 1, (B, (n + 63) // 64), dtype=torch.int64,
-                          device="cuda", generator=gen)
+        T = synth.table_bytes_torch(n, d, z, seed=3, table=i)
+        db.load_async(T, stream)
+        torch.cuda.synchronize()
+        del T
+        R = torch.from_numpy(synth.random_bits(B, n, seed=3, table=i).view(np.int64)).cuda()
         O = torch.empty((B, d * z), dtype=torch.uint8, device="cuda")
         jobs.append((db, B, R, O))
         dbs.append(db)
@@ -762,16 +758,17 @@ def multi_leg(talekpir, synth, torch, stream, args) -> dict:
             "product_tflops_graph": 64.0 * ops / (graph_ms * 1e-3) / 1e12}
 
 
-def large_leg(talekpir, torch, stream, args, hbm_peak) -> dict:
+def large_leg(talekpir, synth, torch, stream, args, hbm_peak) -> dict:
     """n = 2^20 buckets x 4 x 1 KiB (4 GiB): B = 1024 packed request rows in one
     batched pass (the GF(2) product), and single plain reads (HBM stream)."""
     n, d, z, B = 1 << 20, 4, 1024, 1024
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(4)
+    # the same seeded inputs as the parity test of this workload
     db = talekpir.DB(n, d, z)
-    _fill_random(db, n * d * z, gen, torch, stream)
-    R = torch.randint(-(1 << 63), (1 << 63) - 1, (B, n // 64), dtype=torch.int64, device="cuda",
-                      generator=gen)
+    T = synth.table_bytes_torch(n, d, z, seed=0, table=4)
+    db.load_async(T, stream)
+    torch.cuda.synchronize()
+    del T
+    R = torch.from_numpy(synth.random_bits(B, n, seed=4).view(np.int64)).cuda()
     O = torch.empty((B, d * z), dtype=torch.uint8, device="cuda")
     db.read_batch_async(R, B, O, stream)
     bms = _events_ms(torch, stream, lambda: db.read_batch_async(R, B, O, stream), 3)
@@ -843,13 +840,13 @@ def _drive(srv, talekpir, synth, tids, sizes, reqs, msgs, rate, seconds, seed, m
 
 def serve_sweep_leg(talekpir, synth, torch, stream, args) -> dict:
     """Serving under a 64 GiB HBM budget: tables of 2^15..2^18 buckets x 4 x
-    1 KiB are added until the budget refuses one; then open-loop Poisson reads
-    at each rate of --sweep-rates with 10% writes (max 500 evictions, k = 4
-    interest-vector positions in m = 2^20 bits)."""
+    1 KiB (seeded uniform payload) are added until the budget refuses one;
+    then open-loop Poisson reads at each rate of --sweep-rates for
+    --sweep-seconds, with 10% writes (max 500 evictions, k = 4 interest-vector
+    positions in m = 2^20 bits).  Latency runs from each op's scheduled
+    arrival to its completion (no coordinated omission)."""
     m_bits, k = 1 << 20, 4
-    srv = talekpir.Server(hbm_budget_bytes=64 << 30, max_batch=256, max_inflight=2)
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(5)
+    srv = talekpir.Server(hbm_budget_bytes=64 << 30, max_batch=256, max_inflight=4)
     sizes, tids = [], []
     cycle = [1 << 15, 1 << 16, 1 << 17, 1 << 18]
     t_fill = time.perf_counter()
@@ -860,7 +857,10 @@ def serve_sweep_leg(talekpir, synth, torch, stream, args) -> dict:
         except talekpir.TpirError:
             break
         db = srv.table(tid)
-        _fill_random(db, n * 4096, gen, torch, stream)
+        T = synth.table_bytes_torch(n, 4, 1024, seed=5, table=len(tids))   # seeded payload
+        db.load_async(T, stream)
+        torch.cuda.synchronize()
+        del T
         db.bloom_create(m_bits, k, window=4, writes_per_delta=1000)
         sizes.append(n)
         tids.append(tid)
@@ -878,7 +878,11 @@ def serve_sweep_leg(talekpir, synth, torch, stream, args) -> dict:
                     "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms,
                     "reads": st.reads_done, "writes": st.writes_done, "failed": st.failed,
                     "rejected": st.rejected, "launches": st.launches,
-                    "mean_batch": st.mean_batch, "ops": ops})
+                    "mean_batch": st.mean_batch, "ops": ops,
+                    "launches_by_kernel": {"plain": st.kernel_launches[1],
+                                           "lop3": st.kernel_launches[2],
+                                           "four_russians": st.kernel_launches[4],
+                                           "tensor": st.kernel_launches[5]}})
     total = int(sum(n * 4096 for n in sizes))
     srv.close()
     return {"tables": len(sizes), "table_bytes": total, "hbm_budget": 64 << 30,

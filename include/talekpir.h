@@ -327,20 +327,26 @@ tpir_status tpir_rice_encode_async(const uint64_t *d_bits, uint64_t m, int32_t k
                                    uint64_t cap_bytes, uint64_t *d_result, void *stream);
 
 /* ---- serving: continuous batching over resident tables -------------------
- * A server thread admits reads and writes as they arrive, keeps tables
- * resident under an HBM budget, applies each table's writes in arrival order,
- * and launches the waiting reads of all tables together in one persistent
- * launch per tick; up to max_inflight launches overlap on the device.  A read
- * sees every write to its table admitted before the launch that serves it;
- * its completion reports that write count (epoch). */
+ * A server thread admits reads and writes as they arrive into a FIFO per
+ * table, keeps tables resident under an HBM budget, and forms launch units
+ * one table at a time: the table whose oldest waiting op arrived first gets
+ * all its waiting writes applied in arrival order and up to max_batch of its
+ * waiting reads read in one launch after them (the kernel chosen by the
+ * batch, as for tpir_read_batch_async: a table that gathered 48 or more reads
+ * goes to the tensor-core kernel).  A table with no waiting read is never
+ * scanned.  Up to max_inflight units are on the device at once, each table's
+ * in order.  A read sees every write to its table admitted before its unit
+ * was formed; its completion reports that write count (epoch). */
 typedef struct tpir_server tpir_server;
 
 typedef struct {
     uint64_t hbm_budget_bytes; /* tables + staging must fit; 0 = 64 GiB */
     uint32_t max_batch;        /* reads per table per launch (<= 1024); 0 = 256 */
-    uint32_t max_inflight;     /* launches in flight (1..8); 0 = 3 */
+    uint32_t max_inflight;     /* launch units in flight (1..16); 0 = 4 */
     uint32_t queue_capacity;   /* admitted, unfinished ops; 0 = 65536 */
-    uint32_t tick_us;          /* batching interval; 0 = 200 */
+    uint32_t tick_us;          /* batching window: a table's unit is formed once
+                                  its oldest waiting op has waited this long
+                                  or max_batch reads are waiting; 0 = at once */
 } tpir_serve_config;
 
 typedef struct {
@@ -361,6 +367,9 @@ typedef struct {
     double mean_batch;                /* reads per table per launch */
     uint64_t hbm_bytes_in_use;
     uint64_t eviction_hist[8];        /* 0, 1, 2-3, 4-7, ..., >= 64 */
+    uint64_t kernel_launches[6];      /* read launches by kernel (index as in
+                                         tpir_db_set_kernel: 1 plain, 2 register-
+                                         tiled, 4 Four-Russians, 5 tensor-core) */
 } tpir_stats;
 
 tpir_status tpir_serve_create(const tpir_serve_config *cfg, tpir_server **out);

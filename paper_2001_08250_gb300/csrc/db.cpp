@@ -140,7 +140,7 @@ uint32_t next_counter_slot() {
 }
 
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
-                         cudaStream_t st, const uint8_t* d_seeds) {
+                         cudaStream_t st, const uint8_t* d_seeds, int* kernel_used) {
   if (B == 0) return TPIR_OK;
   d_req += db->req_off;  // a row shard reads its own words of each request row
   order_after_writes(db, st);
@@ -157,6 +157,7 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
     else
       kernel = 2;
   }
+  if (kernel_used) *kernel_used = kernel;
   cudaError_t e = cudaSuccess;
   if (kernel == 1 || kernel == 3) {
     const uint32_t* T = reinterpret_cast<const uint32_t*>(db->d_table);

@@ -3,20 +3,26 @@
 // The leader of Section 6 sequences writes and forwards batches of reads; the
 // paper's prototype batches reads before the GPU and notes that reads may be
 // reordered freely while writes must apply in sequence order (Section 9.2).
-// This server does that on one GPU:
-//   - submit_* admit ops into a FIFO (bounded: EAGAIN when full);
-//   - a worker thread forms a launch whenever a pipeline slot is free: it
-//     scans the FIFO in arrival order, applies each table's writes (host
-//     placement + device moves) and collects up to max_batch reads per table;
-//     the collected reads run after the writes of that launch (stream
-//     order): tables with a few reads stream through the plain kernel, all
-//     others share ONE persistent launch of the batched scan kernel;
-//   - up to max_inflight launches are queued on the device at once, with their
-//     request/reply copies on a copy stream overlapping the running kernels,
-//     so reads that arrive while others are on the GPU join the next launch;
-//   - a read sees every write to its table applied before its launch; its
-//     completion reports that write count (epoch).
-// Tables are admitted against an HBM budget (tables + launch staging).
+// This server does that on one GPU, one table at a time:
+//   - submit_* admit ops into the FIFO of their table (bounded in total:
+//     EAGAIN when full);
+//   - a worker thread forms a launch unit whenever a pipeline slot is free:
+//     it picks the table whose oldest waiting op arrived first, applies all of
+//     that table's waiting writes in arrival order (host placement + device
+//     moves) and takes up to max_batch of its waiting reads, which run after
+//     those writes; the read kernel is chosen by the batch (plain stream for a
+//     few reads, the register-tiled kernel, the tensor-core kernel from 48
+//     reads on wide rows), so a table that collected a burst of reads is read
+//     once for all of them;
+//   - a unit never scans a table it has no reads for: a read waits for its own
+//     table's next unit, not for a pass over every resident table;
+//   - up to max_inflight units are queued on the device at once, each table's
+//     units in order on one of a few streams (request and reply copies on the
+//     same stream), so reads that arrive while others are on the GPU join the
+//     next unit of their table;
+//   - a read sees every write to its table admitted before its unit was
+//     formed; its completion reports that write count (epoch).
+// Tables are admitted against an HBM budget (tables + per-slot staging).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -33,8 +39,8 @@ namespace {
 
 using namespace tpir;
 
-// Tables with at most this many reads in a launch use the plain kernel.
-constexpr uint32_t kServePlainMaxB = 4;
+constexpr uint32_t kServeStreams = 4;       // each table's units run in order on one of these
+constexpr uint64_t kSlotStaging = 256ull << 20;  // request + reply staging a slot may grow to
 
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -56,17 +62,14 @@ struct Op {
 
 struct ReadRec {
   uint64_t tag;
-  uint32_t table;
   int64_t t_arrive;
   void* out;
   uint64_t out_off;  // byte offset of the reply in the slot's reply staging
-  uint32_t bytes;
   uint64_t epoch;
 };
 
 struct WriteRec {
   uint64_t tag;
-  uint32_t table;
   int64_t t_arrive;
   tpir_status status;
   uint32_t evictions;
@@ -74,7 +77,7 @@ struct WriteRec {
 };
 
 struct Slot {
-  cudaEvent_t h2d_done = nullptr, kern_done = nullptr, done = nullptr;
+  cudaEvent_t done = nullptr;
   uint64_t* h_req = nullptr;
   uint64_t h_req_cap = 0;
   uint64_t* d_req = nullptr;
@@ -83,16 +86,20 @@ struct Slot {
   uint64_t h_out_cap = 0;
   uint8_t* d_out = nullptr;
   uint64_t d_out_cap = 0;
+  uint32_t table = 0;
+  uint32_t row_bytes = 0;
   std::vector<ReadRec> reads;
   std::vector<WriteRec> writes;
-  std::vector<tpir_write_staging> wstage;  // one per table written in this launch
-  std::vector<tpir_write_staging> bstage;  // Bloom positions, one per table
+  tpir_write_staging wstage;  // write batches too large for the kernel parameters
+  tpir_write_staging bstage;  // Bloom positions
   int64_t t_launch = 0;
 };
 
 struct Table {
   tpir_db* db = nullptr;
   uint64_t bytes = 0;
+  std::deque<Op> ops;  // admitted, not yet in a unit (arrival order)
+  uint64_t nreads = 0; // reads among them
 };
 
 }  // namespace
@@ -100,19 +107,19 @@ struct Table {
 struct tpir_server {
   tpir_serve_config cfg{};
   int device = 0;
-  std::vector<Table> tables;
+  std::deque<Table> tables;  // stable addresses while tables are added
   uint64_t hbm_tables = 0;
   uint64_t staging_reserve = 0;
-  cudaStream_t compute = nullptr, copy = nullptr;
+  cudaStream_t streams[kServeStreams] = {nullptr};
 
   std::mutex mu;
   std::condition_variable cv_work, cv_idle;
-  std::deque<Op> queue;
+  uint64_t queued = 0;      // ops waiting in the tables' FIFOs
   uint64_t unfinished = 0;  // admitted and not yet completed
   bool stop = false;
 
   std::vector<Slot> slots;
-  std::deque<int> inflight;  // slot indices, oldest first
+  std::vector<int> inflight;  // slot indices
   std::vector<int> free_slots;
 
   std::mutex cmu;
@@ -121,6 +128,7 @@ struct tpir_server {
   std::vector<double> lat_ms;
   uint64_t reads_done = 0, writes_done = 0, rejected = 0, failed = 0, launches = 0;
   uint64_t batch_tables = 0, batch_reads = 0;
+  uint64_t kernel_launches[6] = {0};
   int64_t t_first = 0, t_last = 0;
   uint64_t ev_hist[8] = {0};
 
@@ -128,11 +136,6 @@ struct tpir_server {
 };
 
 namespace {
-
-uint64_t slot_staging_bytes(const tpir_serve_config& c) {
-  // request + reply staging a launch may grow to (bounded per slot)
-  return 256ull << 20;
-}
 
 int hist_bucket(uint32_t ev) {
   if (ev == 0) return 0;
@@ -155,7 +158,7 @@ void retire(tpir_server* s, int si) {
     c.tag = w.tag;
     c.status = w.status;
     c.kind = 1;
-    c.table_id = w.table;
+    c.table_id = sl.table;
     c.evictions = w.evictions;
     c.epoch = w.epoch;
     c.t_arrive_ns = w.t_arrive;
@@ -164,12 +167,12 @@ void retire(tpir_server* s, int si) {
     cs.push_back(c);
   }
   for (const ReadRec& r : sl.reads) {
-    std::memcpy(r.out, sl.h_out + r.out_off, r.bytes);
+    std::memcpy(r.out, sl.h_out + r.out_off, sl.row_bytes);
     tpir_completion c{};
     c.tag = r.tag;
     c.status = TPIR_OK;
     c.kind = 0;
-    c.table_id = r.table;
+    c.table_id = sl.table;
     c.epoch = r.epoch;
     c.t_arrive_ns = r.t_arrive;
     c.t_launch_ns = sl.t_launch;
@@ -201,199 +204,186 @@ void retire(tpir_server* s, int si) {
   }
 }
 
-// Forms one launch from the FIFO into slot `si`; returns false if nothing was
-// admitted into it.
-bool form_launch(tpir_server* s, int si) {
+void fail_reads(tpir_server* s, uint32_t t, const std::vector<Op>& reads, tpir_status why) {
+  std::lock_guard<std::mutex> g(s->cmu);
+  for (const Op& op : reads) {
+    tpir_completion c{};
+    c.tag = op.tag;
+    c.status = why;
+    c.table_id = t;
+    c.t_arrive_ns = op.t_arrive;
+    c.t_done_ns = now_ns();
+    s->done.push_back(c);
+    s->failed++;
+  }
+}
+
+// Forms one launch unit into slot `si`: among the tables whose ops are ready
+// (the oldest has waited the batching window, tick_us, or max_batch reads are
+// waiting), the one whose oldest waiting op arrived first; all its waiting
+// writes and up to max_batch of its reads.  Returns false if no table is
+// ready; *next_ready_ns then tells when the earliest one will be (0: none).
+bool form_unit(tpir_server* s, int si, int64_t* next_ready_ns) {
   Slot& sl = s->slots[si];
-  std::vector<Op> taken_writes;
-  std::unordered_map<uint32_t, std::vector<Op>> reads_by_table;
-  std::vector<uint32_t> table_order;
+  std::vector<Op> writes, reads;
+  uint32_t t = 0;
+  Table* tab = nullptr;
+  *next_ready_ns = 0;
   {
     std::lock_guard<std::mutex> g(s->mu);
-    if (s->queue.empty()) return false;
-    std::unordered_map<uint32_t, uint32_t> count;
-    std::deque<Op> keep;
-    uint32_t njobs = 0;
-    while (!s->queue.empty()) {
-      Op op = std::move(s->queue.front());
-      s->queue.pop_front();
-      if (op.kind == 1) {
-        taken_writes.push_back(std::move(op));
-        continue;
-      }
-      auto it = count.find(op.table);
-      const bool new_table = it == count.end();
-      if ((new_table && njobs >= TPIR_MAX_JOBS) ||
-          (!new_table && it->second >= s->cfg.max_batch)) {
-        keep.push_back(std::move(op));
-        continue;
-      }
-      if (new_table) {
-        count[op.table] = 1;
-        ++njobs;
-        table_order.push_back(op.table);
+    if (s->queued == 0) return false;
+    const int64_t now = now_ns(), window = static_cast<int64_t>(s->cfg.tick_us) * 1000;
+    int64_t oldest = INT64_MAX, soonest = INT64_MAX;
+    bool found = false;
+    for (uint32_t i = 0; i < s->tables.size(); ++i) {
+      const Table& x = s->tables[i];
+      if (x.ops.empty()) continue;
+      const int64_t ta = x.ops.front().t_arrive;
+      if (s->stop || now - ta >= window || x.nreads >= s->cfg.max_batch) {
+        if (ta < oldest) {
+          oldest = ta;
+          t = i;
+          found = true;
+        }
       } else {
-        it->second++;
+        soonest = std::min(soonest, ta + window);
       }
-      reads_by_table[op.table].push_back(std::move(op));
     }
-    s->queue.swap(keep);
+    if (!found) {
+      *next_ready_ns = soonest == INT64_MAX ? 0 : soonest;
+      return false;
+    }
+    tab = &s->tables[t];
+    std::deque<Op> keep;
+    while (!tab->ops.empty()) {
+      Op op = std::move(tab->ops.front());
+      tab->ops.pop_front();
+      if (op.kind == 1)
+        writes.push_back(std::move(op));
+      else if (reads.size() < s->cfg.max_batch)
+        reads.push_back(std::move(op));
+      else
+        keep.push_back(std::move(op));
+    }
+    tab->ops.swap(keep);
+    tab->nreads -= reads.size();
+    s->queued -= writes.size() + reads.size();
   }
+  tpir_db* db = tab->db;
+  cudaStream_t st = s->streams[t % kServeStreams];
+  sl.table = t;
+  sl.row_bytes = db->row_bytes;
   sl.t_launch = now_ns();
 
-  // ---- writes, per table in arrival order, on the compute stream
-  std::unordered_map<uint32_t, std::vector<size_t>> wtab;
-  std::vector<uint32_t> worder;
-  for (size_t i = 0; i < taken_writes.size(); ++i) {
-    const uint32_t t = taken_writes[i].table;
-    if (!wtab.count(t)) worder.push_back(t);
-    wtab[t].push_back(i);
-  }
-  if (sl.wstage.size() < worder.size()) sl.wstage.resize(worder.size());
-  if (sl.bstage.size() < worder.size()) sl.bstage.resize(worder.size());
-  for (size_t wi = 0; wi < worder.size(); ++wi) {
-    const uint32_t t = worder[wi];
-    tpir_db* db = s->tables[t].db;
-    const auto& idx = wtab[t];
-    std::vector<uint64_t> b1(idx.size()), b2(idx.size()), pos;
-    std::vector<uint8_t> msgs(idx.size() * db->z);
-    uint32_t with_bloom = 0;
-    for (size_t j = 0; j < idx.size(); ++j) {
-      const Op& op = taken_writes[idx[j]];
-      b1[j] = op.b1;
-      b2[j] = op.b2;
-      std::memcpy(msgs.data() + j * db->z, op.msg.data(), db->z);
+  // ---- writes, in arrival order
+  if (!writes.empty()) {
+    const size_t nw = writes.size();
+    std::vector<uint64_t> b1(nw), b2(nw), pos;
+    std::vector<uint8_t> msgs(nw * db->z);
+    for (size_t j = 0; j < nw; ++j) {
+      b1[j] = writes[j].b1;
+      b2[j] = writes[j].b2;
+      std::memcpy(msgs.data() + j * db->z, writes[j].msg.data(), db->z);
     }
-    std::vector<tpir_status> st(idx.size(), TPIR_OK);
-    std::vector<uint32_t> ev(idx.size(), 0);
+    std::vector<tpir_status> stv(nw, TPIR_OK);
+    std::vector<uint32_t> ev(nw, 0);
     const uint64_t epoch0 = db->epoch;
-    tpir_status r = apply_writes_core(db, static_cast<uint32_t>(idx.size()), b1.data(), b2.data(),
-                                      msgs.data(), st.data(), ev.data(), s->compute, sl.wstage[wi]);
+    order_writes_after_reads(db, st);
+    const tpir_status r = apply_writes_core(db, static_cast<uint32_t>(nw), b1.data(), b2.data(),
+                                            msgs.data(), stv.data(), ev.data(), st, sl.wstage);
     uint64_t e = epoch0;
-    for (size_t j = 0; j < idx.size(); ++j) {
-      const Op& op = taken_writes[idx[j]];
-      const tpir_status sj = (r != TPIR_OK) ? r : st[j];
+    uint32_t with_bloom = 0;
+    for (size_t j = 0; j < nw; ++j) {
+      const Op& op = writes[j];
+      const tpir_status sj = (r != TPIR_OK) ? r : stv[j];
       if (sj == TPIR_OK) ++e;
-      sl.writes.push_back(WriteRec{op.tag, t, op.t_arrive, sj, ev[j], e});
+      sl.writes.push_back(WriteRec{op.tag, op.t_arrive, sj, r != TPIR_OK ? 0u : ev[j], e});
       if (sj == TPIR_OK && db->bloom.d_deltas && op.bloom.size() == db->bloom.k) {
         pos.insert(pos.end(), op.bloom.begin(), op.bloom.end());
         ++with_bloom;
       }
     }
-    if (with_bloom) bloom_insert_core(db, pos.data(), with_bloom, s->compute, sl.bstage[wi]);
+    if (with_bloom) bloom_insert_core(db, pos.data(), with_bloom, st, sl.bstage);
   }
 
-  // ---- reads: pack requests and reply offsets per table
-  uint64_t req_words = 0, out_bytes = 0;
-  for (uint32_t t : table_order) {
-    tpir_db* db = s->tables[t].db;
-    const uint64_t B = reads_by_table[t].size();
-    req_words += B * db->words64;
-    out_bytes += (B * db->row_bytes + 255) / 256 * 256;
-  }
-  if (!table_order.empty()) {
-    if (!grow_pinned(reinterpret_cast<void**>(&sl.h_req), &sl.h_req_cap, req_words * 8) ||
-        !grow_dev(reinterpret_cast<void**>(&sl.d_req), &sl.d_req_cap, req_words * 8) ||
+  // ---- reads: one launch for all of them, after the writes
+  if (!reads.empty()) {
+    const uint32_t B = static_cast<uint32_t>(reads.size());
+    const uint64_t req_bytes = static_cast<uint64_t>(B) * db->words64 * 8;
+    const uint64_t out_bytes = static_cast<uint64_t>(B) * db->row_bytes;
+    if (!grow_pinned(reinterpret_cast<void**>(&sl.h_req), &sl.h_req_cap, req_bytes) ||
+        !grow_dev(reinterpret_cast<void**>(&sl.d_req), &sl.d_req_cap, req_bytes) ||
         !grow_pinned(reinterpret_cast<void**>(&sl.h_out), &sl.h_out_cap, out_bytes) ||
         !grow_dev(reinterpret_cast<void**>(&sl.d_out), &sl.d_out_cap, out_bytes)) {
-      // cannot stage: fail these reads
-      for (uint32_t t : table_order)
-        for (const Op& op : reads_by_table[t]) {
-          tpir_completion c{};
-          c.tag = op.tag;
-          c.status = TPIR_ENOMEM;
-          c.table_id = t;
-          c.t_arrive_ns = op.t_arrive;
-          c.t_done_ns = now_ns();
-          std::lock_guard<std::mutex> g(s->cmu);
-          s->done.push_back(c);
-          s->failed++;
-        }
-      table_order.clear();
+      fail_reads(s, t, reads, TPIR_ENOMEM);
+      std::lock_guard<std::mutex> g(s->mu);
+      s->unfinished -= reads.size();
+      reads.clear();
     }
-  }
-  std::vector<tpir_read_job> jobs;
-  uint64_t wo = 0, oo = 0;
-  for (uint32_t t : table_order) {
-    tpir_db* db = s->tables[t].db;
-    auto& ops = reads_by_table[t];
-    const uint32_t B = static_cast<uint32_t>(ops.size());
-    for (uint32_t b = 0; b < B; ++b) {
-      std::memcpy(sl.h_req + wo + static_cast<uint64_t>(b) * db->words64, ops[b].req.data(),
+    for (uint32_t b = 0; b < reads.size(); ++b) {
+      std::memcpy(sl.h_req + static_cast<uint64_t>(b) * db->words64, reads[b].req.data(),
                   db->words64 * 8);
-      sl.reads.push_back(ReadRec{ops[b].tag, t, ops[b].t_arrive, ops[b].out,
-                                 oo + static_cast<uint64_t>(b) * db->row_bytes, db->row_bytes,
-                                 db->epoch});
+      sl.reads.push_back(ReadRec{reads[b].tag, reads[b].t_arrive, reads[b].out,
+                                 static_cast<uint64_t>(b) * db->row_bytes, db->epoch});
     }
-    jobs.push_back(tpir_read_job{db, B, sl.d_req + wo, sl.d_out + oo});
-    wo += static_cast<uint64_t>(B) * db->words64;
-    oo += (static_cast<uint64_t>(B) * db->row_bytes + 255) / 256 * 256;
-  }
-  if (!jobs.empty()) {
-    cudaMemcpyAsync(sl.d_req, sl.h_req, req_words * 8, cudaMemcpyHostToDevice, s->copy);
-    cudaEventRecord(sl.h2d_done, s->copy);
-    cudaStreamWaitEvent(s->compute, sl.h2d_done, 0);
-    // tables with a few reads are HBM-bound: stream each with the plain
-    // kernel (back-to-back launches overlap); the rest share one persistent
-    // launch of the batched kernel
-    std::vector<tpir_read_job> batched;
-    for (const tpir_read_job& j : jobs) {
-      if (j.B <= kServePlainMaxB)
-        enqueue_read(j.db, j.d_req_bits, j.B, j.d_out, s->compute);
-      else
-        batched.push_back(j);
+    if (!reads.empty()) {
+      int kernel = 0;
+      cudaMemcpyAsync(sl.d_req, sl.h_req, req_bytes, cudaMemcpyHostToDevice, st);
+      const tpir_status r = enqueue_read(db, sl.d_req, B, sl.d_out, st, nullptr, &kernel);
+      cudaMemcpyAsync(sl.h_out, sl.d_out, out_bytes, cudaMemcpyDeviceToHost, st);
+      std::lock_guard<std::mutex> g(s->cmu);
+      s->launches++;
+      s->batch_tables++;
+      s->batch_reads += B;
+      if (r == TPIR_OK && kernel > 0 && kernel < 6) s->kernel_launches[kernel]++;
     }
-    if (!batched.empty())
-      enqueue_multi(batched.data(), static_cast<uint32_t>(batched.size()), s->compute);
-    cudaEventRecord(sl.kern_done, s->compute);
-    cudaStreamWaitEvent(s->copy, sl.kern_done, 0);
-    cudaMemcpyAsync(sl.h_out, sl.d_out, out_bytes, cudaMemcpyDeviceToHost, s->copy);
-    cudaEventRecord(sl.done, s->copy);
-    std::lock_guard<std::mutex> g(s->cmu);
-    s->launches++;
-    s->batch_tables += jobs.size();
-    s->batch_reads += sl.reads.size();
-  } else {
-    // writes only: completion follows the compute stream
-    cudaEventRecord(sl.done, s->compute);
   }
+  cudaEventRecord(sl.done, st);
   return true;
 }
 
 void worker_main(tpir_server* s) {
   cudaSetDevice(s->device);
   for (;;) {
-    // retire finished launches, oldest first
-    while (!s->inflight.empty()) {
-      const int si = s->inflight.front();
-      if (cudaEventQuery(s->slots[si].done) != cudaSuccess) break;
-      s->inflight.pop_front();
-      retire(s, si);
-      s->free_slots.push_back(si);
+    // retire finished units (units of different tables may finish in any order)
+    for (size_t i = 0; i < s->inflight.size();) {
+      const int si = s->inflight[i];
+      if (cudaEventQuery(s->slots[si].done) == cudaSuccess) {
+        retire(s, si);
+        s->free_slots.push_back(si);
+        s->inflight.erase(s->inflight.begin() + static_cast<long>(i));
+      } else {
+        ++i;
+      }
     }
     bool pending;
     {
       std::lock_guard<std::mutex> g(s->mu);
-      pending = !s->queue.empty();
+      pending = s->queued > 0;
       if (s->stop && !pending && s->inflight.empty()) break;
     }
+    int64_t next_ready = 0;
     if (pending && !s->free_slots.empty()) {
       const int si = s->free_slots.back();
       s->free_slots.pop_back();
-      if (form_launch(s, si))
+      if (form_unit(s, si, &next_ready)) {
         s->inflight.push_back(si);
-      else
-        s->free_slots.push_back(si);
-      continue;
+        continue;
+      }
+      s->free_slots.push_back(si);
     }
     if (!s->inflight.empty()) {
-      // a launch is running: poll its completion without burning a core
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      // units are running: poll their completion without burning a core
+      std::this_thread::sleep_for(std::chrono::microseconds(10));
       continue;
     }
+    // idle: sleep until an op arrives, the earliest waiting table's batching
+    // window ends, or the server stops
     std::unique_lock<std::mutex> lk(s->mu);
-    s->cv_work.wait_for(lk, std::chrono::microseconds(s->cfg.tick_us),
-                        [&] { return s->stop || !s->queue.empty(); });
+    const int64_t wait_ns = next_ready ? std::max<int64_t>(next_ready - now_ns(), 1000) : 1000000;
+    const uint64_t q0 = s->queued;
+    s->cv_work.wait_for(lk, std::chrono::nanoseconds(wait_ns),
+                        [&] { return s->stop || s->queued != q0; });
   }
 }
 
@@ -409,27 +399,24 @@ tpir_status tpir_serve_create(const tpir_serve_config* cfg, tpir_server** out) {
   if (cfg) s->cfg = *cfg;
   if (!s->cfg.hbm_budget_bytes) s->cfg.hbm_budget_bytes = 64ull << 30;
   if (!s->cfg.max_batch) s->cfg.max_batch = 256;
-  if (!s->cfg.max_inflight) s->cfg.max_inflight = 2;
+  if (!s->cfg.max_inflight) s->cfg.max_inflight = 4;
   if (!s->cfg.queue_capacity) s->cfg.queue_capacity = 65536;
-  if (!s->cfg.tick_us) s->cfg.tick_us = 200;
-  if (s->cfg.max_batch > 1024 || s->cfg.max_inflight > 8) {
+  if (s->cfg.max_batch > 1024 || s->cfg.max_inflight > 16) {
     delete s;
     return TPIR_EINVAL;
   }
   cudaGetDevice(&s->device);
-  s->staging_reserve = s->cfg.max_inflight * slot_staging_bytes(s->cfg);
+  s->staging_reserve = s->cfg.max_inflight * kSlotStaging;
   if (s->staging_reserve >= s->cfg.hbm_budget_bytes) {
     delete s;
     return TPIR_ENOMEM;
   }
-  cudaError_t e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+  cudaError_t e = cudaSuccess;
+  for (uint32_t i = 0; i < kServeStreams && e == cudaSuccess; ++i)
+    e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
   s->slots.resize(s->cfg.max_inflight);
   for (uint32_t i = 0; i < s->cfg.max_inflight && e == cudaSuccess; ++i) {
-    Slot& sl = s->slots[i];
-    e = cudaEventCreateWithFlags(&sl.h2d_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.kern_done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    e = cudaEventCreateWithFlags(&s->slots[i].done, cudaEventDisableTiming);
     s->free_slots.push_back(static_cast<int>(i));
   }
   if (e != cudaSuccess) {
@@ -450,7 +437,9 @@ tpir_status tpir_serve_add_table(tpir_server* s, uint64_t n, uint32_t d, uint32_
   if (s->hbm_tables + bytes + s->staging_reserve > s->cfg.hbm_budget_bytes) return TPIR_ENOMEM;
   tpir_db* db = tpir_db_create(n, d, msg_bytes);
   if (!db) return tpir_last_error();
-  s->tables.push_back(Table{db, bytes});
+  s->tables.emplace_back();
+  s->tables.back().db = db;
+  s->tables.back().bytes = bytes;
   s->hbm_tables += bytes;
   *table_id = static_cast<uint32_t>(s->tables.size() - 1);
   return TPIR_OK;
@@ -473,7 +462,10 @@ static tpir_status admit(tpir_server* s, Op&& op) {
     return TPIR_EAGAIN;
   }
   s->unfinished++;
-  s->queue.push_back(std::move(op));
+  s->queued++;
+  Table& t = s->tables[op.table];
+  if (op.kind == 0) t.nreads++;
+  t.ops.push_back(std::move(op));
   s->cv_work.notify_one();
   return TPIR_OK;
 }
@@ -559,6 +551,7 @@ tpir_status tpir_serve_stats(tpir_server* s, tpir_stats* st) {
     if (s->t_last > s->t_first)
       st->reads_per_s = s->reads_done / ((s->t_last - s->t_first) * 1e-9);
     for (int i = 0; i < 8; ++i) st->eviction_hist[i] = s->ev_hist[i];
+    for (int i = 0; i < 6; ++i) st->kernel_launches[i] = s->kernel_launches[i];
     lat = s->lat_ms;
   }
   if (!lat.empty()) {
@@ -587,6 +580,7 @@ tpir_status tpir_serve_reset_stats(tpir_server* s) {
   s->batch_tables = s->batch_reads = 0;
   s->t_first = s->t_last = 0;
   for (auto& h : s->ev_hist) h = 0;
+  for (auto& k : s->kernel_launches) k = 0;
   return TPIR_OK;
 }
 
@@ -598,22 +592,20 @@ tpir_status tpir_serve_destroy(tpir_server* s) {
     s->cv_work.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
-  if (s->compute) cudaStreamSynchronize(s->compute);
-  if (s->copy) cudaStreamSynchronize(s->copy);
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamSynchronize(st);
   for (Slot& sl : s->slots) {
     if (sl.h_req) cudaFreeHost(sl.h_req);
     if (sl.h_out) cudaFreeHost(sl.h_out);
     cudaFree(sl.d_req);
     cudaFree(sl.d_out);
-    for (auto& w : sl.wstage) w.release();
-    for (auto& w : sl.bstage) w.release();
-    if (sl.h2d_done) cudaEventDestroy(sl.h2d_done);
-    if (sl.kern_done) cudaEventDestroy(sl.kern_done);
+    sl.wstage.release();
+    sl.bstage.release();
     if (sl.done) cudaEventDestroy(sl.done);
   }
   for (Table& t : s->tables) tpir_db_destroy(t.db);
-  if (s->compute) cudaStreamDestroy(s->compute);
-  if (s->copy) cudaStreamDestroy(s->copy);
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamDestroy(st);
   delete s;
   return TPIR_OK;
 }

@@ -322,8 +322,11 @@ tpir_status set_error(tpir_status s);
 tpir_status cuda_status(cudaError_t e);
 // enqueue a read of db on stream (device buffers), honoring write ordering;
 // d_seeds (B x 32 bytes) masks the replies (serialized PIR), null = plain
+// (*kernel_used, if given, receives the kernel chosen: 1 plain, 2 register-
+// tiled, 3 plain register-streaming, 4 Four-Russians, 5 tensor-core)
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
-                         cudaStream_t st, const uint8_t* d_seeds = nullptr);
+                         cudaStream_t st, const uint8_t* d_seeds = nullptr,
+                         int* kernel_used = nullptr);
 // order stream `st` after the db's last write, and record a read event
 void order_after_writes(tpir_db* db, cudaStream_t st);
 void note_read(tpir_db* db, cudaStream_t st);

@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("failed", _u64), ("launches", _u64), ("reads_per_s", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("mean_batch", ctypes.c_double),
-                ("hbm_bytes_in_use", _u64), ("eviction_hist", _u64 * 8)]
+                ("hbm_bytes_in_use", _u64), ("eviction_hist", _u64 * 8),
+                ("kernel_launches", _u64 * 6)]
 
 
 # (name, restype, argtypes) for every entry point of include/talekpir.h

@@ -199,31 +199,6 @@ def test_multi_table_tensor_launch_chunks_and_request_paths():
     assert talekpir.device_status() == talekpir.OK
 
 
-def test_large_table_gf2_product_sampled():
-    """n = 2^20, d = 4, 1 KiB messages (4 GiB), B = 1024 packed request rows:
-    sampled rows plus a Freivalds check of the whole product, for the batched
-    kernel and, on a few rows, the plain kernel."""
-    require_cuda()
-    n, d, z, B = 1 << 20, 4, 1024, 1024
-    T = synth.table_bytes(n, d, z, seed=0, table=4)
-    R = synth.random_bits(B, n, seed=4)
-    with _db(n, d, z, T) as db:
-        dR, dO = to_dev(R), dev_out(B, d * z)
-        db.read_batch_async(dR, B, dO)
-        Out = to_host(dO)
-        check_rows(T, n, d, z, R, Out, [0, 511, 1023])
-        freivalds(T, n, d, z, R, Out, trials=8, seed=44)
-        db.set_kernel(PLAIN)
-        dO1 = dev_out(4, d * z)
-        db.read_batch_async(dR, 4, dO1)
-        assert np.array_equal(to_host(dO1), Out[:4])
-        db.set_kernel(M4RM)
-        dO4 = dev_out(B, d * z)
-        db.read_batch_async(dR, B, dO4)
-        assert np.array_equal(to_host(dO4), Out)
-    assert talekpir.device_status() == talekpir.OK
-
-
 def test_multi_table_graph_replays_see_writes():
     """The many-table read captured into a CUDA graph: replays give the oracle's
     replies, and a replay after a write to one table sees that write."""

@@ -202,6 +202,61 @@ def test_serve_mix_each_result_same_alone_and_in_mix():
     srv.close()
 
 
+def test_serve_bursts_reach_the_tensor_core_kernel():
+    """Reads arrive in bursts of 300 per table with writes between them.  With
+    a batching window (tick_us) a table's burst is read in launches of up to
+    max_batch = 256 requests, which take the tensor-core kernel (48 or more
+    requests on rows of 256 bytes or more); the rest of each burst takes the
+    register-tiled kernel.  Every read equals the oracle's answer on the table
+    state its completion reports, and the server's launch counts show the
+    tensor-core kernel ran inside the serve loop."""
+    require_cuda()
+    shapes = [(4096, 4, 1024), (3000, 2, 256)]
+    seeds = [61, 62]
+    srv = talekpir.Server(hbm_budget_bytes=8 << 30, max_batch=256, max_inflight=2,
+                          tick_us=20000)
+    for (n, d, z), sd in zip(shapes, seeds):
+        tid = srv.add_table(n, d, z)
+        srv.table(tid).set_policy(0, 500, sd)
+    writes = {0: [], 1: []}
+    reads, outs = {}, {}
+    tag = 0
+    for burst in range(3):
+        for t, (n, d, z) in enumerate(shapes):
+            keys = synth.write_keys(5, seed=700 + 10 * burst + t)
+            b1, b2 = synth.bucket_pairs(keys, n)
+            msgs = synth.messages(5, z, seed=800 + 10 * burst + t)
+            for j in range(5):
+                writes[t].append((int(b1[j]), int(b2[j]), msgs[j]))
+                assert srv.submit_write(t, int(b1[j]), int(b2[j]), msgs[j], tag) == talekpir.OK
+                tag += 1
+            R = synth.random_bits(300, n, seed=900 + 10 * burst + t)
+            for q in R:
+                outs[tag] = np.empty(d * z, dtype=np.uint8)
+                reads[tag] = (t, q)
+                assert srv.submit_read(t, q, outs[tag], tag) == talekpir.OK
+                tag += 1
+        srv.drain()
+    comps = srv.poll(100000)
+    assert len(comps) == tag
+    assert all(c.status == 0 for c in comps)
+    st = srv.stats()
+    assert st.reads_done == len(reads)
+    assert st.kernel_launches[5] >= 2, list(st.kernel_launches)
+    assert st.mean_batch >= 48
+    cache = {}
+    for c in comps:
+        if c.kind != 0:
+            continue
+        t, q = reads[c.tag]
+        key = (t, c.epoch)
+        if key not in cache:
+            cache[key] = _replay(shapes[t], seeds[t], writes[t], c.epoch)
+        n, d, z = shapes[t]
+        assert np.array_equal(outs[c.tag], oracle.read(cache[key], n, d, z, q)), c.tag
+    srv.close()
+
+
 def test_serve_budget_and_backpressure():
     require_cuda()
     srv = talekpir.Server(hbm_budget_bytes=1 << 30, max_batch=8, max_inflight=2, queue_capacity=4)
