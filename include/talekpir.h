@@ -221,7 +221,11 @@ tpir_status tpir_xor_combine(const void *const *d_srcs, uint32_t count, uint64_t
  * 4 = batched Four-Russians kernel (groups of 8 buckets, 256 combinations in
  * shared memory, one lookup per request and group), 5 = batched tensor-core
  * kernel (the GF(2) product as an exact integer product of 0/1 matrices on
- * tcgen05, e4m3 operands, fp32 accumulators, reduced mod 2). */
+ * tcgen05: packed 4-bit e2m1 operands with unit block scales, fp32
+ * accumulators, reduced mod 2).  The tensor-core kernel reads a
+ * bit-transposed copy of the table (each column's bits over 64 buckets in
+ * one word; as large as the table), allocated and built by the first read
+ * that uses it and then kept equal to the table by every write and load. */
 tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
 
 /* Autotuner of the batched kernel's tile shape: times every admissible shape

@@ -139,24 +139,23 @@ uint32_t next_counter_slot() {
   return next.fetch_add(1, std::memory_order_relaxed) % kItemCounterSlots;
 }
 
+int auto_kernel(const tpir_db* db, uint32_t B) {
+  if (db->forced_kernel) return db->forced_kernel;
+  // plain stream for a few requests; the tensor-core kernel once its
+  // 128-request M-tiles are well filled (measured crossover with the
+  // register-tiled kernel on GB300); the register-tiled kernel in between
+  if (B <= kPlainMaxB) return 1;
+  if (B >= kTensorMinB && db->Wd >= 64) return 5;
+  return 2;
+}
+
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
-                         cudaStream_t st, const uint8_t* d_seeds, int* kernel_used) {
+                         cudaStream_t st, const uint8_t* d_seeds, int* kernel_used,
+                         int kernel_choice) {
   if (B == 0) return TPIR_OK;
   d_req += db->req_off;  // a row shard reads its own words of each request row
   order_after_writes(db, st);
-  int kernel = db->forced_kernel;
-  if (kernel == 0) {
-    // plain stream for a few requests; the tensor-core kernel once its
-    // 128-request M-tiles are well filled (measured crossover with the
-    // register-tiled kernel on GB300: B ~ 96 for 4 KiB rows); the
-    // register-tiled kernel in between
-    if (B <= kPlainMaxB)
-      kernel = 1;
-    else if (B >= kTensorMinB && db->Wd >= 64)
-      kernel = 5;
-    else
-      kernel = 2;
-  }
+  const int kernel = kernel_choice ? kernel_choice : auto_kernel(db, B);
   if (kernel_used) *kernel_used = kernel;
   cudaError_t e = cudaSuccess;
   if (kernel == 1 || kernel == 3) {
@@ -171,8 +170,10 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
                        kernel == 3 ? -1 : 0);
     }
   } else if (kernel == 5) {
-    e = launch_gf2_mma(reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, d_req,
-                       db->words64, B, reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
+    e = tcopy_ensure(db, st);
+    if (e == cudaSuccess)
+      e = launch_gf2_mma(db->d_tt, db->n, db->Wd, d_req, db->words64, B,
+                         reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
   } else if (kernel == 4) {
     e = launch_m4rm(reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, d_req,
                     db->words64, B, reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
@@ -238,6 +239,7 @@ tpir_status apply_writes_core(tpir_db* db, uint32_t count, const uint64_t* b1, c
       std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
       std::memcpy(m.payload, msgs, pay_bytes);
       e = launch_apply_moves_param(db->d_table, db->z, m, db->d_tmp, st);
+      if (e == cudaSuccess) e = tcopy_after_moves(db, ops.data(), ops.size(), st);
     } else {
       const uint64_t ops_bytes = ops.size() * sizeof(MoveOp);
       if (!grow_pinned(reinterpret_cast<void**>(&stg.h), &stg.h_cap, pay_bytes + ops_bytes) ||
@@ -256,6 +258,7 @@ tpir_status apply_writes_core(tpir_db* db, uint32_t count, const uint64_t* b1, c
         e = launch_apply_moves(db->d_table, db->z, stg.d_ops, static_cast<uint32_t>(ops.size()),
                                stg.d_payload, db->d_tmp, st);
       if (e == cudaSuccess) e = cudaEventRecord(stg.done, st);
+      if (e == cudaSuccess) e = tcopy_after_moves(db, ops.data(), ops.size(), st);
     }
     if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
     if (e != cudaSuccess) {
@@ -306,6 +309,16 @@ tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, 
   return cuda_status(e);
 }
 
+// The kernel a job of a many-table launch takes: 4 Four-Russians (forced),
+// 5 tensor-core (forced, or 48 or more requests on rows of 256 bytes or
+// more), else 2 register-tiled.
+int multi_kernel(const tpir_read_job& q) {
+  const int forced = q.db->forced_kernel;
+  if (forced == 4 && q.db->Wd >= 64) return 4;
+  if (forced == 5 || (forced == 0 && q.B >= kTensorMinB && q.db->Wd >= 64)) return 5;
+  return 2;
+}
+
 tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st) {
   // large batches on rows of >= 256 bytes: one launch of the tensor-core
   // kernel (a db forced to the Four-Russians kernel: its launches, 512-request
@@ -324,13 +337,18 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
                       q.d_req_bits + q.db->req_off, q.db->words64, q.B,
                       reinterpret_cast<uint32_t*>(q.d_out),
                       static_cast<const uint8_t*>(q.d_seeds)};
-    const int forced = q.db->forced_kernel;
-    if (forced == 4 && q.db->Wd >= 64)
+    const int kind = multi_kernel(q);
+    if (kind == 4) {
       (q.B > 256 ? m4w : m4).push_back(r);
-    else if (forced == 5 || (forced == 0 && q.B >= kTensorMinB && q.db->Wd >= 64))
-      tc.push_back(r);
-    else
+    } else if (kind == 5) {
+      const cudaError_t e = tcopy_ensure(q.db, st);
+      if (e != cudaSuccess) return cuda_status(e);
+      M4Request t = r;
+      t.Tt = q.db->d_tt;
+      tc.push_back(t);
+    } else {
       lop3.push_back(q);
+    }
   }
   tpir_status s = enqueue_multi_lop3(lop3.data(), static_cast<uint32_t>(lop3.size()), st);
   if (s == TPIR_OK && !tc.empty())
@@ -521,6 +539,7 @@ void tpir_db_destroy(tpir_db* db) {
   cudaFree(db->d_table);
   db->stage.release();
   cudaFree(db->d_tmp);
+  cudaFree(db->d_tt);
   cudaFree(db->d_req);
   cudaFree(db->d_out);
   cudaFree(db->bloom.d_deltas);
@@ -571,6 +590,7 @@ tpir_status tpir_db_load(tpir_db* db, const void* host_table, size_t bytes) {
   if (e != cudaSuccess) return cuda_status(e);
   order_writes_after_reads(db, db->stream);
   e = cudaMemcpyAsync(db->d_table, host_table, bytes, cudaMemcpyHostToDevice, db->stream);
+  if (e == cudaSuccess) e = tcopy_after_load(db, db->stream);
   if (e == cudaSuccess) e = cudaEventRecord(db->last_write, db->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
   if (e != cudaSuccess) return cuda_status(e);
@@ -585,6 +605,7 @@ tpir_status tpir_db_load_async(tpir_db* db, const void* src, size_t bytes, void*
   cudaError_t e = cudaEventRecord(db->stream_mark, db->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, db->stream_mark, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_table, src, bytes, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = tcopy_after_load(db, st);
   if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
   if (e != cudaSuccess) return cuda_status(e);
   db->meta->clear();
@@ -792,6 +813,21 @@ tpir_status tpir_read_multi_graph_create(const tpir_read_job* jobs, uint32_t njo
   tpir_graph* g = new (std::nothrow) tpir_graph();
   if (!g) return TPIR_ENOMEM;
   (void)batched_grid();  // one-time kernel attributes, outside the capture
+  // the tensor-core jobs' transposed copies exist before the capture (their
+  // allocation and first build cannot be captured); later writes and loads
+  // keep them current in stream order
+  for (uint32_t i = 0; i < njobs; ++i) {
+    if (!jobs[i].B || multi_kernel(jobs[i]) != 5) continue;
+    tpir_db* db = jobs[i].db;
+    order_writes_after_reads(db, db->stream);
+    cudaError_t e = cudaStreamWaitEvent(db->stream, db->last_write, 0);
+    if (e == cudaSuccess) e = tcopy_ensure(db, db->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(db->last_write, db->stream);
+    if (e != cudaSuccess) {
+      delete g;
+      return cuda_status(e);
+    }
+  }
   cudaStream_t st = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);

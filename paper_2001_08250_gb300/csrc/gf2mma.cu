@@ -2,52 +2,59 @@
 // Section 9.2): Out = R (x) T over GF(2).  Each output bit is the parity of
 // an integer: the number of buckets k with request bit R[b][k] = 1 and table
 // bit T[k][c] = 1.  The kernel computes these integers exactly as a product
-// of 0/1 matrices on the 5th-generation tensor cores (tcgen05.mma,
-// kind::f8f6f4, e4m3 operands, fp32 accumulators in tensor memory) and keeps
-// the low bit of each: exactly the XOR of the selected buckets, with every
-// bucket read for every request as in the scalar kernels.
+// of 0/1 matrices on the 5th-generation tensor cores and keeps the low bit of
+// each: exactly the XOR of the selected buckets, with every bucket read for
+// every request as in the scalar kernels.
 //
-// Shapes.  An item is (256-bit column strip of the table = 8 words of every
-// row, block of up to 256 requests = two M-tiles of 128, k-chunk of buckets).
-// The MMA is M = 128 requests x N = 256 columns x K = 32 buckets.
+// Operands.  Both matrices are 4-bit e2m1 values (a set bit = 1.0, packed two
+// per byte) in the block-scaled MMA (tcgen05.mma kind::mxf4, every scale
+// factor 1.0 = UE8M0 0x7F), accumulated in fp32 in tensor memory: products
+// are 0 or 1 and a k-chunk's counts stay <= 32 768, exact in fp32.  Packed
+// 4-bit operands are taken only K-major, so the table is read from its
+// bit-transposed copy (tcopy.cu: for each column, 64 buckets' bits in one
+// word), and the request rows are K-major by nature.  Half the operand bytes
+// of an 8-bit form per multiply-add: the shared-memory traffic that bounds
+// this kernel (expander stores, MMA operand reads) halves with them.
 //
-// Data flow per CTA (persistent, one per SM, 576 threads):
-//   warp 16     streams the strip (8 words of 128 rows per stage) with 2-D TMA
-//               loads into a ring of raw stages, ahead of use, and with them
-//               the stage's request words (2 words of each of the item's
-//               requests) when their rows can be staged: rows of an even
-//               number of 64-bit words as rows, of an odd number as row
-//               pairs (TMA boxes start 16-byte aligned);
-//   warps 0-3   table producers: each takes 32 rows of a raw stage, one row
-//               per lane, and writes the row's 256 bits as e4m3 bytes (a set
-//               bit = 2^-6) into the B operand, which is MN-major (columns
-//               contiguous), so a table row needs no transposition (buckets
-//               and columns take the shared order of g_spread);
-//   warps 4-7   request producers: expand each request's 128 bits of the
-//               stage into the other operand, from the raw stage (staged
-//               rows) or from global memory three stages ahead;
-//   warp 17 lane 0 issues the MMAs of each stage into the item's accumulators
-//               and commits them to the stage's "empty" barrier;
-//   warps 8-15  epilogue: read the accumulators (tcgen05.ld), take each sum's
+// Shapes.  An item is (strip of 224 table columns = 7 reply words, block of up
+// to 256 requests = two M-tiles of 128, k-chunk of buckets).  The MMA is M =
+// 128 requests x N = 224 columns x K = 64 buckets; a pipeline stage holds 256
+// buckets (4 request / table words).  Tensor memory: 2 x 224 accumulator
+// columns (two M-tiles of one item, or one M-tile of two items
+// double-buffered) and the scale factors in columns 448..511.
+//
+// Data flow per CTA (persistent, one per SM, 672 threads):
+//   warp 11     streams, by 2-D TMA, each stage's 4 words of the strip's 224
+//               columns of the transposed table and the stage's 4 words of
+//               the item's requests into a ring of raw stages: rows of an
+//               even number of 64-bit words as rows, of an odd number as row
+//               pairs (TMA boxes start 16-byte aligned); per-thread loads for
+//               a request buffer that is not 16-byte aligned;
+//   warps 0-6   table expanders: lane = column; its 256 bits of the stage
+//               become 128 bytes of e2m1 (the column's row of the B operand);
+//   warps 7-10  request expanders: lane = two requests (q, 128 + q); their
+//               256 bits each become the A operand rows;
+//   warp 20     one thread issues the MMAs of each stage and commits them to
+//               the stage's "empty" barrier;
+//   warps 12-19 epilogue: read the accumulators (tcgen05.ld), take each sum's
 //               parity, and store (single k-chunk) or XOR-reduce (split, or a
 //               masked read) the reply words; two groups of four warps split
-//               an item (one M-tile, or half the strip's words, each), so the
-//               tensor pipe waits half as long when one item's accumulators
-//               fill the tensor memory.
-// Stages: 3 x 64 KiB ring (A: 2 x 128 requests x 128 buckets, K-major; B:
-// 256 columns x 128 buckets, MN-major).  Accumulators: 2 x 256 TMEM columns (two M-tiles of one
-// item, or two items of one M-tile each, double-buffered).  Every wait is
-// bounded; a wait that gives up sets the status word, the CTA drains its MMAs
-// and frees its tensor memory before it returns.
+//               an item (one M-tile, or four / three of its seven words).
+// Both operands use one order of the buckets within a 32-bucket chunk:
+// element 8 t + m of the chunk (nibble m of its 32-bit word t) is bucket
+// 4 m + t, so a word's 32 bits become their 32 nibbles with one shift and
+// one mask per 8 nibbles.  Every wait is bounded; a wait that gives up sets
+// the status word, and the CTA drains its MMAs and TMA loads and frees its
+// tensor memory before it returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <atomic>
 #include <map>
-#include <vector>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "chacha.cuh"
 #include "mbar.cuh"
@@ -56,49 +63,56 @@
 namespace tpir {
 namespace {
 
-constexpr int kGStages = 3;
-constexpr int kGKStage = 128;                    // buckets per stage
-constexpr int kGKStep = 32;                      // buckets per MMA (32 e4m3 bytes of K)
-constexpr int kGWords = 8;                       // table words per strip (256 columns)
-constexpr int kGTile = 128 * kGKStage;           // 128 operand rows of one stage: 16 KiB
-constexpr int kGStageBytes = 4 * kGTile;         // A: 2 tiles, B: 2 tiles
-constexpr int kGSbo = (kGKStage / 16) * 128;     // A: bytes between 8-row core-matrix groups
-constexpr int kGLbo = 128;                       // A: bytes between 16-byte K chunks
-constexpr int kGSboB = (kGKStage / 8) * 128;     // B: bytes between 16-column groups
-constexpr int kGLboB = 128;                      // B: bytes between 8-bucket K groups
-constexpr int kGThreads = 576;                   // 18 warps (roles in the kernel)
-constexpr uint32_t kGTmaWarp = 16, kGIssueWarp = 17;
-constexpr int kGRawTable = 128 * kGWords * 4;    // table strip: 128 rows x 8 words, 4 KiB
-// Raw stages (table strip + request words) by request-staging mode RM:
-// RM = 0 or 1: 256 request rows x 16 bytes; RM = 2 (rows of an odd number
-// of words, staged as row pairs): 128 even rows x 16 bytes, then 128 odd
-// rows x 32 bytes (a 4-word box from the even word before the stage's two).
+constexpr int kGStages = 3;                      // operand ring
+constexpr int kGKStage = 256;                    // buckets per stage
+constexpr int kGStageWords = kGKStage / 64;      // 64-bit words of a request row / table column per stage
+constexpr int kGKStep = 64;                      // buckets per MMA
+constexpr int kGCols = 224;                      // table columns per strip (MMA N)
+constexpr int kGStripWords = kGCols / 32;        // reply words per strip
+constexpr int kGRowBytes = kGKStage / 2;         // operand bytes per row per stage (e2m1)
+constexpr int kGTileA = 128 * kGRowBytes;        // 128 request rows: 16 KiB
+constexpr int kGTileB = kGCols * kGRowBytes;     // 224 column rows: 28 KiB
+constexpr int kGStageBytes = 2 * kGTileA + kGTileB;
+// K-major, no swizzle: 8-row x 16-byte core matrices, kGLbo apart along K,
+// kGSbo apart along M / N.  Row r, byte k of an operand: (r / 8) kGSbo +
+// (k / 16) kGLbo + (r % 8) 16.
+constexpr int kGLbo = 128;
+constexpr int kGSbo = (kGRowBytes / 16) * 128;
+constexpr uint32_t kGTableWarps = 7, kGReqWarp0 = 7, kGReqWarps = 4;
+constexpr uint32_t kGTmaWarp = 11, kGEpiWarp0 = 12, kGIssueWarp = 20;
+constexpr int kGThreads = 21 * 32;
+constexpr int kGRawTable = kGCols * kGStageWords * 8;  // 4 words of 224 columns: 7 KiB
+// Raw stages (table words + request words) by request-staging mode RM:
+// RM = 1: 256 request rows x 32 bytes; RM = 2 (rows of an odd number of
+// words, staged as row pairs): 128 even rows x 32 bytes, then 128 odd rows x
+// 48 bytes (a 6-word box from the even word before the stage's four); RM = 0:
+// the table words only (requests loaded by the expanders).
 template <int RM>
-__host__ __device__ constexpr int g_raw_req() { return RM == 2 ? 128 * 16 + 128 * 32 : 256 * 16; }
+__host__ __device__ constexpr int g_raw_req() { return RM == 1 ? 256 * 32 : RM == 2 ? 128 * 32 + 128 * 48 : 0; }
 template <int RM>
-__host__ __device__ constexpr int g_raw_stages() { return RM == 2 ? 3 : 4; }
+__host__ __device__ constexpr int g_raw_stages() { return RM == 1 ? 3 : RM == 2 ? 2 : 6; }
 template <int RM>
 __host__ __device__ constexpr int g_raw_bytes() { return kGRawTable + g_raw_req<RM>(); }
 template <int RM>
 __host__ __device__ constexpr int g_smem() { return 1024 + kGStages * kGStageBytes + g_raw_stages<RM>() * g_raw_bytes<RM>(); }
-static_assert(g_smem<1>() <= 232448 && g_smem<2>() <= 232448, "dynamic shared memory above 227 KiB");
+static_assert(g_smem<0>() <= 231424 && g_smem<1>() <= 231424 && g_smem<2>() <= 231424,
+              "dynamic shared memory above 227 KiB less the static part");
 constexpr uint32_t kGTmemCols = 512;
+constexpr uint32_t kGSfCol = 448;                // scale factors: columns 448..511 (UE8M0 1.0)
+constexpr uint32_t kGSfa = 448, kGSfb = 480;
 constexpr uint64_t kGWaitNs = 4000000000ull;
-constexpr int kGIssuers = 1;                     // MMA-issuing threads
-constexpr uint32_t kGOne = 0x08u;                // e4m3 2^-6: the value of a set bit
 constexpr uint64_t kGMaxCount = 32768;           // largest count one accumulator holds
 
 // Descriptor increments (start address in 16-byte units): one stage, one
-// 128-row A tile, one K-step of A (two 16-byte K chunks), one K-step of B
-// (four 8-bucket K groups).
+// 128-row A tile, one K-step (two 16-byte chunks).
 constexpr uint64_t kDescStage = kGStageBytes >> 4;
-constexpr uint64_t kDescTile = kGTile >> 4;
-constexpr uint64_t kDescKa = (2 * kGLbo) >> 4;
-constexpr uint64_t kDescKb = (4 * kGLboB) >> 4;
+constexpr uint64_t kDescTile = kGTileA >> 4;
+constexpr uint64_t kDescK = (2 * kGLbo) >> 4;
 
-// Instruction descriptor: D fp32, A and B e4m3, A K-major, B MN-major (bit
-// 16), N = 256, M = 128.
-constexpr uint32_t kGIdesc = (1u << 4) | (1u << 16) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor of the block-scaled MMA: A and B e2m1 (1), both
+// K-major, N = 224, UE8M0 scales (bit 23), M = 128, scale-factor ids 0.
+constexpr uint32_t kGIdesc = (1u << 7) | (1u << 10) | ((uint32_t)(kGCols >> 3) << 17) | (1u << 23) |
+                             ((128u >> 4) << 24);
 
 // One table's read in a launch (one job of a many-table launch).
 struct GJob {
@@ -117,7 +131,8 @@ struct GJob {
 };
 
 // A launch: NJ jobs (one for a single-table read), each with the tensor maps
-// of its table and (req_tma) of its request rows, in the kernel parameters.
+// of its transposed table and (req_tma) of its request rows, in the kernel
+// parameters.
 template <int NJ>
 struct GLaunch {
   CUtensorMap maps[NJ];
@@ -173,9 +188,9 @@ __device__ __forceinline__ uint32_t g_item_of(uint32_t r) {
 }
 
 // This CTA's items in order.  Item mode: items c, ... of the launch list
-// (g_item_of).  Span mode (one job with at most about one k-chunk of stages
-// per CTA): the job's stages are ordered (M-block, strip, stage) and cut into
-// one contiguous span per CTA of equal length; an item is a run of the span
+// (g_item_of).  Span mode (one job with at most one k-chunk of stages per
+// CTA): the job's stages are ordered (M-block, strip, stage) and cut into one
+// contiguous span per CTA of equal length; an item is a run of the span
 // within one strip and one k-chunk of kGMaxCount buckets (chunks aligned to
 // multiples of kGMaxCount), so a CTA runs one or two items (accumulator
 // read-outs).
@@ -244,42 +259,23 @@ __device__ __forceinline__ void g_cur_next(GCursor& c, const GLaunch<NJ>& L) {
   if (c.ks >= c.it.k1) g_cur_item(c, L);
 }
 
-// Shared-memory matrix descriptors without swizzle.  K-major (A): 8-row x
-// 16-byte core matrices, kGLbo apart along K, kGSbo apart along M.  MN-major
-// (B): 16-column x 8-bucket core matrices (each bucket's 16 columns
-// contiguous), kGLboB apart along K, kGSboB apart along N.
-__device__ __forceinline__ uint64_t g_desc_sw(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(lbo >> 4) << 16) |
-         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
-}
-__device__ __forceinline__ uint64_t g_desc(uint32_t addr) { return g_desc_sw(addr, kGLbo, kGSbo); }
-__device__ __forceinline__ uint64_t g_desc_b(uint32_t addr) { return g_desc_sw(addr, kGLboB, kGSboB); }
-
-// byte offset of (row, k) in the K-major A operand of a stage
-__device__ __forceinline__ uint32_t g_off(uint32_t row, uint32_t kbyte) {
-  return (row >> 3) * kGSbo + (kbyte >> 4) * kGLbo + (row & 7u) * 16u;
-}
-// byte offset of (16-column group g, bucket k) in the MN-major B operand
-__device__ __forceinline__ uint32_t g_off_b(uint32_t g, uint32_t k) {
-  return g * kGSboB + (k >> 3) * kGLboB + (k & 7u) * 16u;
+// Shared-memory matrix descriptor, K-major without swizzle.
+__device__ __forceinline__ uint64_t g_desc(uint32_t addr) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>(kGLbo >> 4) << 16) |
+         (static_cast<uint64_t>(kGSbo >> 4) << 32) | (1ull << 46);
 }
 
-// Operand order within a K-step of 32 buckets (and within a word of 32 table
-// columns): byte 4m + j of the K-step (or of the 32 columns) holds bit m + 8j
-// of the word.  The product sums over K, so any order both operands share is
-// the same product; this one turns a word into its 32 e4m3 bytes (kGOne where
-// the bit is set) with one shift and one mask per 4 bytes.  The epilogue
-// undoes the column order when it packs the parities.
-__device__ __forceinline__ void g_spread(uint32_t x, uint4& lo, uint4& hi) {
-  static_assert(kGOne == 0x08u, "each bit lands on bit 3 of its byte");
-  constexpr uint32_t m = kGOne * 0x01010101u;
-  lo = make_uint4((x << 3) & m, (x << 2) & m, (x << 1) & m, x & m);
-  hi = make_uint4((x >> 1) & m, (x >> 2) & m, (x >> 3) & m, (x >> 4) & m);
+// byte offset of (row, 16-byte chunk) in an operand tile of a stage
+__device__ __forceinline__ uint32_t g_off(uint32_t row, uint32_t chunk) {
+  return (row >> 3) * kGSbo + chunk * kGLbo + (row & 7u) * 16u;
 }
-// Bucket (0..31 within its K-step) held by K position p of the K-step: the
-// table expanders read that row, so that each lane stores to K position p and
-// a warp's operand stores stay contiguous (bank-conflict free)
-__device__ __forceinline__ uint32_t g_kbucket(uint32_t p) { return (p >> 2) + 8u * (p & 3u); }
+
+// 32 buckets' bits (bit i = bucket i of the chunk) as 32 e2m1 nibbles, 1.0
+// (0x2) where set: nibble m of word t is bucket 4 m + t.
+__device__ __forceinline__ uint4 g_spread(uint32_t h) {
+  constexpr uint32_t m = 0x22222222u;
+  return make_uint4((h << 1) & m, h & m, (h >> 1) & m, (h >> 2) & m);
+}
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
@@ -287,9 +283,9 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
                : "memory");
 }
 
-__device__ __forceinline__ uint2 ld_shared_v2(uint32_t addr) {
-  uint2 v;
-  asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr) : "memory");
+__device__ __forceinline__ uint64_t ld_shared_u64(uint32_t addr) {
+  uint64_t v;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
   return v;
 }
 
@@ -313,35 +309,38 @@ __device__ __forceinline__ void g_tma_load(uint32_t dst, const CUtensorMap* map,
       : "memory");
 }
 
-// the request words of one stage: this thread's request in each M-tile,
-// buckets ks .. ks + 127 (zeros past the request rows and the batch)
+// the request words of one stage for this thread's request in each M-tile
+// (zeros past the job's words and the batch), loaded from global memory
 template <int NJ>
 __device__ __forceinline__ void g_req_load(const GLaunch<NJ>& L, const GCursor& c, uint32_t q,
-                                           uint64_t (&x)[4]) {
-  const uint64_t wi = c.ks >> 6;
+                                           uint64_t (&x)[8]) {
 #pragma unroll
-  for (uint32_t t = 0; t < 2; ++t) x[2 * t] = x[2 * t + 1] = 0ull;
+  for (int i = 0; i < 8; ++i) x[i] = 0ull;
   if (!c.valid) return;
   const GJob& J = L.jobs[c.it.job];
+  const uint64_t wi = c.ks >> 6;
+  // the job's own words end at ceil(n / 64): a row shard's request rows are
+  // longer (words64 is the stride) and go on with other shards' words
+  const uint64_t nw = (J.n + 63) / 64;
 #pragma unroll
   for (uint32_t t = 0; t < 2; ++t) {
     const uint32_t b = c.it.b0 + 128u * t + q;
     if (t < c.it.mt && b < J.B) {
       const uint64_t* rq = J.R + static_cast<uint64_t>(b) * J.words64;
-      x[2 * t] = __ldg(rq + wi);
-      // the job's own words end at ceil(n / 64): a row shard's request rows
-      // are longer (words64 is the stride) and end with other shards' words
-      if (wi + 1 < (J.n + 63) / 64) x[2 * t + 1] = __ldg(rq + wi + 1);
+#pragma unroll
+      for (uint32_t i = 0; i < kGStageWords; ++i)
+        if (wi + i < nw) x[4 * t + i] = __ldg(rq + wi + i);
     }
   }
 }
 
 __device__ __forceinline__ void g_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                      uint32_t accumulate) {
+                                      uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(kGIdesc), "r"(accumulate)
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], "
+      "p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kGIdesc), "r"(sfa), "r"(sfb), "r"(accumulate)
       : "memory");
 }
 
@@ -351,23 +350,8 @@ __device__ __forceinline__ void g_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void g_red_xor64(uint32_t* p, uint32_t lo, uint32_t hi) {
-  const uint64_t v = (static_cast<uint64_t>(hi) << 32) | lo;
-  asm volatile("red.relaxed.gpu.global.xor.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Parity word of the 32 accumulator columns of one table word: each value is
-// an exact count times 2^-12; scaling by 2^12 and adding 2^23 puts the count
-// in the mantissa, whose lowest bit is the count's parity.  Column v of the
-// word holds table bit 4 (v >> 4) + ((v >> 2) & 3) + 8 (v & 3) (the operand
-// order of g_spread).
-__device__ __forceinline__ uint32_t g_parity_word(const uint32_t (&r)[32]) {
-  uint32_t w = 0;
-#pragma unroll
-  for (int v = 0; v < 32; ++v)
-    w |= (__float_as_uint(fmaf(__uint_as_float(r[v]), 4096.f, 8388608.f)) & 1u)
-         << (4 * (v >> 4) + ((v >> 2) & 3) + 8 * (v & 3));
-  return w;
+__device__ __forceinline__ void g_red_xor32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.xor.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void g_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -383,50 +367,49 @@ __device__ __forceinline__ void g_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Parity words of NC consecutive table words (w0 ..) for request b from the
-// accumulator columns at taddr, written (or XOR-reduced, for a split k range
-// or masked replies) into the reply row.  Reply rows are whole 16-byte words.
-template <int NC>
-__device__ __forceinline__ void g_epilogue(const GJob& J, uint32_t taddr, uint32_t b, uint32_t w0) {
-  uint32_t pw[NC];
+// Parity words of `nw` (<= 7) consecutive reply words (w0 ..) for request b
+// from the accumulator columns at taddr (column 32 c + j = bit j of word
+// w0 + c): each value is an exact count; adding 2^23 puts it in the
+// mantissa, whose lowest bit is the count's parity.  Written, or XOR-reduced
+// for a split k range or masked replies, into the reply row.
+__device__ __forceinline__ void g_epilogue(const GJob& J, uint32_t taddr, uint32_t b, uint32_t w0,
+                                           uint32_t nw) {
+  uint32_t pw[kGStripWords];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
+  for (uint32_t c = 0; c < kGStripWords; ++c) {
     pw[c] = 0u;
-    if (w0 + c < J.Wd) {  // uniform across the warp
+    if (c < nw && w0 + c < J.Wd) {  // uniform across the warp
       uint32_t v[32];
       g_ld32(taddr + 32u * c, v);
-      pw[c] = g_parity_word(v);
+      uint32_t w = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        w |= (__float_as_uint(__uint_as_float(v[j]) + 8388608.0f) & 1u) << j;
+      pw[c] = w;
     }
   }
   if (b >= J.B) return;
   uint32_t* o = J.out + static_cast<uint64_t>(b) * J.Wd + w0;
-  if (J.split) {
 #pragma unroll
-    for (int c = 0; c < NC; c += 2) {
-      if (w0 + c + 1 < J.Wd)
-        g_red_xor64(o + c, pw[c], pw[c + 1]);
-      else if (w0 + c < J.Wd)
-        atomicXor(o + c, pw[c]);
+  for (uint32_t c = 0; c < kGStripWords; ++c) {
+    if (c < nw && w0 + c < J.Wd) {
+      if (J.split)
+        g_red_xor32(o + c, pw[c]);
+      else
+        o[c] = pw[c];
     }
-  } else if (w0 + NC <= J.Wd) {
-#pragma unroll
-    for (int c = 0; c < NC; c += 4)
-      reinterpret_cast<uint4*>(o)[c / 4] = make_uint4(pw[c], pw[c + 1], pw[c + 2], pw[c + 3]);
-  } else {
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (w0 + c < J.Wd) o[c] = pw[c];
   }
 }
 
-// One stage of the request operand: waits for the stage slot, writes this
-// thread's request in each M-tile (128 bits of the stage as e4m3 bytes,
-// K-major) and marks its part of the stage full.  False if the CTA aborted.
+// The request operand of one stage: this thread's request in each M-tile
+// (the stage's 256 bits as e2m1, K-major), written once the stage slot is
+// free, then this warp's arrival on the stage's "full" barrier.  False if
+// the CTA aborted.
 template <int NJ>
 __device__ __forceinline__ bool g_req_stage(const GLaunch<NJ>& L, const GCursor& c,
-                                            const uint64_t (&x)[4], uint32_t iter, uint32_t q,
-                                            uint32_t stage0, uint64_t* full, uint64_t* empty,
-                                            volatile int* abort_flag, int* status) {
+                                            const uint64_t (&x)[8], uint32_t iter, uint32_t q,
+                                            uint32_t lane, uint32_t stage0, uint64_t* full,
+                                            uint64_t* empty, volatile int* abort_flag, int* status) {
   const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
   if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) return false;
   const uint32_t st = stage0 + s * kGStageBytes;
@@ -434,65 +417,66 @@ __device__ __forceinline__ bool g_req_stage(const GLaunch<NJ>& L, const GCursor&
   for (uint32_t t = 0; t < 2; ++t) {
     const uint32_t b = c.it.b0 + 128u * t + q;
     if (t < c.it.mt && b < L.jobs[c.it.job].B) {
-      const uint32_t xw[4] = {static_cast<uint32_t>(x[2 * t]), static_cast<uint32_t>(x[2 * t] >> 32),
-                              static_cast<uint32_t>(x[2 * t + 1]), static_cast<uint32_t>(x[2 * t + 1] >> 32)};
-      const uint32_t abase = st + t * kGTile + g_off(q, 0);
+      const uint32_t o = st + t * kGTileA + g_off(q, 0);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {  // K-step k: buckets ks + 32 k .. ks + 32 k + 31
-        uint4 lo, hi;
-        g_spread(xw[k], lo, hi);
-        st_shared_v4(abase + (2 * k) * kGLbo, lo);
-        st_shared_v4(abase + (2 * k + 1) * kGLbo, hi);
+      for (uint32_t i = 0; i < kGStageWords; ++i) {  // K-step i: buckets ks + 64 i ..
+        st_shared_v4(o + (2 * i) * kGLbo, g_spread(static_cast<uint32_t>(x[4 * t + i])));
+        st_shared_v4(o + (2 * i + 1) * kGLbo, g_spread(static_cast<uint32_t>(x[4 * t + i] >> 32)));
       }
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mb::arrive(&full[s]);
+  __syncwarp();
+  if (lane == 0) mb::arrive(&full[s]);
   return true;
 }
 
-// One stage of a request expander: the stage's words (RM = 1: from the raw
-// stage, else the preloaded x), the operand (g_req_stage), then (RM = 1) the
-// raw slot's release.  False if the CTA aborted.
+// One stage of a request expander: the stage's words (RM 1 / 2: from the raw
+// stage, whose slot goes back to the TMA warp as soon as the words are in
+// registers; RM 0: the preloaded x), then the operand (g_req_stage).  False
+// if the CTA aborted.
 template <int NJ, int RM>
 __device__ __forceinline__ bool g_req_step(const GLaunch<NJ>& L, const GCursor& c,
-                                           const uint64_t (&x)[4], uint32_t iter, uint32_t q,
+                                           const uint64_t (&x)[8], uint32_t iter, uint32_t q,
                                            uint32_t lane, uint32_t stage0, uint32_t raw0,
                                            uint64_t* full, uint64_t* empty, uint64_t* raw_full,
                                            uint64_t* raw_empty, volatile int* abort_flag,
                                            int* status) {
   constexpr int kGRaw = g_raw_stages<RM>(), kGRawBytes = g_raw_bytes<RM>();
   if constexpr (RM == 0) {
-    return g_req_stage(L, c, x, iter, q, stage0, full, empty, abort_flag, status);
+    return g_req_stage(L, c, x, iter, q, lane, stage0, full, empty, abort_flag, status);
   } else {
     const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
     if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) return false;
     const uint32_t base = raw0 + rs * kGRawBytes + kGRawTable;
-    uint64_t y[4];
-    if constexpr (RM == 1) {
-      const uint4 v0 = ld_shared_v4(base + q * 16u), v1 = ld_shared_v4(base + (128u + q) * 16u);
-      y[0] = v0.x | static_cast<uint64_t>(v0.y) << 32;
-      y[1] = v0.z | static_cast<uint64_t>(v0.w) << 32;
-      y[2] = v1.x | static_cast<uint64_t>(v1.y) << 32;
-      y[3] = v1.z | static_cast<uint64_t>(v1.w) << 32;
-    } else {
-      // request 128 t + q of the block: even rows' words at their pair's 16
-      // bytes, odd rows' at bytes 8 .. 23 of their pair's 32
+    uint64_t y[8];
 #pragma unroll
-      for (uint32_t t = 0; t < 2; ++t) {
+    for (uint32_t t = 0; t < 2; ++t) {
+      if constexpr (RM == 1) {
+        const uint32_t a = base + (128u * t + q) * 32u;
+        const uint4 v0 = ld_shared_v4(a), v1 = ld_shared_v4(a + 16u);
+        y[4 * t + 0] = v0.x | static_cast<uint64_t>(v0.y) << 32;
+        y[4 * t + 1] = v0.z | static_cast<uint64_t>(v0.w) << 32;
+        y[4 * t + 2] = v1.x | static_cast<uint64_t>(v1.y) << 32;
+        y[4 * t + 3] = v1.z | static_cast<uint64_t>(v1.w) << 32;
+      } else {
+        // request 128 t + q of the block: even rows' words at their pair's
+        // 32 bytes, odd rows' at bytes 8 .. 39 of their pair's 48
         const uint32_t pr = 64u * t + (q >> 1);
-        const uint32_t a = (q & 1u) ? base + 128u * 16u + pr * 32u + 8u : base + pr * 16u;
-        const uint2 lo = ld_shared_v2(a), hi = ld_shared_v2(a + 8u);
-        y[2 * t] = lo.x | static_cast<uint64_t>(lo.y) << 32;
-        y[2 * t + 1] = hi.x | static_cast<uint64_t>(hi.y) << 32;
+        const uint32_t a = (q & 1u) ? base + 128u * 32u + pr * 48u + 8u : base + pr * 32u;
+#pragma unroll
+        for (uint32_t i = 0; i < kGStageWords; ++i) y[4 * t + i] = ld_shared_u64(a + 8u * i);
       }
     }
-    // the words are consumed (operand stores, then a proxy fence) before
-    // the slot is released
-    if (!g_req_stage(L, c, y, iter, q, stage0, full, empty, abort_flag, status)) return false;
+    // the words are in registers (the fence depends on them) and ordered
+    // before the async proxy's next write to the slot, then the slot is free
+    uint32_t used = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) used ^= static_cast<uint32_t>(y[i]) ^ static_cast<uint32_t>(y[i] >> 32);
+    asm volatile("fence.proxy.async.shared::cta;" ::"r"(used) : "memory");
     __syncwarp();
     if (lane == 0) mb::arrive(&raw_empty[rs]);
-    return true;
+    return g_req_stage(L, c, y, iter, q, lane, stage0, full, empty, abort_flag, status);
   }
 }
 
@@ -519,22 +503,22 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kGStages; ++s) {
-      mb::init(&full[s], 256);
-      mb::init(&empty[s], kGIssuers);
+      mb::init(&full[s], kGTableWarps + kGReqWarps);  // one arrival per expander warp
+      mb::init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
-      mb::init(&accf[b], kGIssuers);
+      mb::init(&accf[b], 1);
       mb::init(&acce[b], 256);
     }
-    mb::init(&drain, kGIssuers);
+    mb::init(&drain, 1);
     for (int s = 0; s < kGRaw; ++s) {
       mb::init(&raw_full[s], 1);
-      mb::init(&raw_empty[s], RM == 0 ? 4 : 8);  // table (+ request) expander warps
+      mb::init(&raw_empty[s], RM == 0 ? kGTableWarps : kGTableWarps + kGReqWarps);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == kGEpiWarp0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      mb::saddr(&s_tmem)),
                  "r"(kGTmemCols)
@@ -545,9 +529,24 @@ __global__ void __launch_bounds__(kGThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
+  if (warp >= kGEpiWarp0 && warp < kGEpiWarp0 + 4) {
+    // scale factors of every MMA: UE8M0 1.0 in columns 448..511 of this
+    // warp's 32 lanes
+    const uint32_t one = 0x7F7F7F7Fu;
+    for (uint32_t col = kGSfCol; col < kGTmemCols; col += 8)
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
+              tmem + (((warp & 3u) * 32u) << 16) + col),
+          "r"(one)
+          : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (warp == kGTmaWarp) {
-    // ------------------------- table strip loads (TMA) -------------------------
+    // ---------------- transposed-table words and request words (TMA) ----------------
     if (lane == 0) {
       uint32_t p = 0;
       for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++p) {
@@ -555,26 +554,29 @@ __global__ void __launch_bounds__(kGThreads, 1)
         if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
         const uint32_t dst = raw0 + rs * kGRawBytes;
         const GJob& J = L.jobs[c.it.job];
-        const uint32_t rbytes = RM == 1 ? J.req_box * 16u : RM == 2 ? J.req_box * 16u + J.req_box_o * 32u : 0u;
+        const uint32_t rbytes =
+            RM == 1 ? J.req_box * 32u : RM == 2 ? J.req_box * 32u + J.req_box_o * 48u : 0u;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
                          mb::saddr(&raw_full[rs])),
                      "r"(kGRawTable + rbytes)
                      : "memory");
-        g_tma_load(dst, &L.maps[c.it.job], static_cast<int>(c.it.strip * kGWords),
-                   static_cast<int>(c.ks), &raw_full[rs]);
-        // the stage's 128 request bits of the item's 256 requests (rows past
-        // the batch read as zeros)
+        // 4 words of the strip's 224 columns (zeros past the row and the table)
+        g_tma_load(dst, &L.maps[c.it.job], static_cast<int>(c.it.strip * kGCols),
+                   static_cast<int>(c.ks >> 6), &raw_full[rs]);
+        const int wi = static_cast<int>(c.ks >> 6);
         if constexpr (RM == 1) {
-          g_tma_load(dst + kGRawTable, &L.rmaps[c.it.job], static_cast<int>(c.ks >> 6),
-                     static_cast<int>(c.it.b0), &raw_full[rs]);
+          // 4 words of each of the item's (up to) 256 requests (rows past the
+          // batch and words past the job's read as zeros)
+          g_tma_load(dst + kGRawTable, &L.rmaps[c.it.job], wi, static_cast<int>(c.it.b0),
+                     &raw_full[rs]);
         } else if constexpr (RM == 2) {
-          // row pairs: even rows' two words at word ks/64 of the pair, odd
-          // rows' four words from the word before theirs (even, so the box
-          // starts 16-byte aligned); words past the pair read as zeros
-          const int wi = static_cast<int>(c.ks >> 6), py = static_cast<int>(c.it.b0 >> 1);
+          // row pairs: even rows' four words at word ks/64 of the pair, odd
+          // rows' six words from the word before theirs (even, so the box
+          // starts 16-byte aligned)
+          const int py = static_cast<int>(c.it.b0 >> 1);
           g_tma_load(dst + kGRawTable, &L.rmaps[c.it.job], wi, py, &raw_full[rs]);
           if (J.req_box_o)
-            g_tma_load(dst + kGRawTable + 128 * 16, &L.rmaps_o[c.it.job],
+            g_tma_load(dst + kGRawTable + 128 * 32, &L.rmaps_o[c.it.job],
                        static_cast<int>(J.words64) + wi - 1, py, &raw_full[rs]);
         }
       }
@@ -592,67 +594,64 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
       }
     }
-  } else if (warp < 4) {
+  } else if (warp < kGTableWarps) {
     // ------------------------ table expanders ------------------------
+    // lane = column 32 warp + lane of the strip: its 4 words of the stage
+    // (buckets ks .. ks + 255) become its 128-byte row of the B operand
+    const uint32_t col = 32u * warp + lane;
     uint32_t iter = 0;
     for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter) {
       const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
       const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
       if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) break;
-      // row ks + 32 warp + g_kbucket(lane) of the strip (zeros past the table:
-      // TMA fill), stored at K position 32 warp + lane
-      const uint32_t ra = raw0 + rs * kGRawBytes + (32u * warp + g_kbucket(lane)) * (kGWords * 4);
-      const uint4 a = ld_shared_v4(ra), b = ld_shared_v4(ra + 16);
-      if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
-      uint32_t used = 0;
-      if (c.ks + 32u * warp < c.it.k1) {
-        const uint32_t w[kGWords] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        const uint32_t o =
-            stage0 + s * kGStageBytes + 2 * kGTile + g_off_b(0, 32u * warp + lane);
+      const uint32_t rb = raw0 + rs * kGRawBytes + col * 8u;
+      uint64_t x[kGStageWords];
 #pragma unroll
-        for (int i = 0; i < kGWords; ++i) {  // word i: columns 32 i .. 32 i + 31
-          uint4 lo, hi;
-          g_spread(w[i], lo, hi);
-          st_shared_v4(o + (2 * i) * kGSboB, lo);
-          st_shared_v4(o + (2 * i + 1) * kGSboB, hi);
-        }
-      } else {
-        used = a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+      for (int i = 0; i < kGStageWords; ++i) x[i] = ld_shared_u64(rb + i * (kGCols * 8));
+      {
+        // the raw slot goes back once the words are in registers and ordered
+        // before the async proxy's next write to it
+        uint32_t used = 0;
+#pragma unroll
+        for (int i = 0; i < kGStageWords; ++i)
+          used ^= static_cast<uint32_t>(x[i]) ^ static_cast<uint32_t>(x[i] >> 32);
+        asm volatile("fence.proxy.async.shared::cta;" ::"r"(used) : "memory");
+        __syncwarp();
+        if (lane == 0) mb::arrive(&raw_empty[rs]);
       }
-      // The raw slot goes back to the TMA warp only once this warp's loads
-      // from it have landed (their values are consumed above) and are ordered
-      // before the async proxy's next write to the slot: a shared load still
-      // in flight at the release could read the next stage's rows.
-      asm volatile("fence.proxy.async.shared::cta;" ::"r"(used) : "memory");
+      if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
+      const uint32_t o = stage0 + s * kGStageBytes + 2 * kGTileA + g_off(col, 0);
+#pragma unroll
+      for (int i = 0; i < kGStageWords; ++i) {
+        st_shared_v4(o + (2 * i) * kGLbo, g_spread(static_cast<uint32_t>(x[i])));
+        st_shared_v4(o + (2 * i + 1) * kGLbo, g_spread(static_cast<uint32_t>(x[i] >> 32)));
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mb::arrive(&raw_empty[rs]);
-      mb::arrive(&full[s]);
+      if (lane == 0) mb::arrive(&full[s]);
     }
-  } else if (warp < 8 && RM != 0) {
+  } else if (warp < kGReqWarp0 + kGReqWarps && RM != 0) {
     // ------------------- request expanders (TMA-staged words) -------------------
-    // Thread q takes requests q and 128 + q of the item's (up to) 256: the TMA
-    // warp lands each stage's request words next to its table rows, one shared
-    // load per request and stage (a strided global load per request and stage
-    // would cost the load/store pipe a wavefront per thread).
-    const uint32_t q = threadIdx.x - 128u;
+    // Thread q takes requests q and 128 + q of the item's (up to) 256.
+    const uint32_t q = threadIdx.x - 32u * kGReqWarp0;
     uint32_t iter = 0;
-    const uint64_t none[4] = {0, 0, 0, 0};
+    const uint64_t none[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter)
       if (!g_req_step<NJ, RM>(L, c, none, iter, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
                              abort_flag, status))
         break;
-  } else if (warp < 8) {
+  } else if (warp < kGReqWarp0 + kGReqWarps) {
     // ------------------------ request expanders ------------------------
     // Thread q takes requests q and 128 + q of the item's (up to) 256, loaded
     // from global memory into three register sets, each loaded three stages
     // ahead of its use so that a stage does not wait on their (L2) latency.
-    const uint32_t q = threadIdx.x - 128u;
+    const uint32_t q = threadIdx.x - 32u * kGReqWarp0;
     GCursor ca = g_cur_start(L);
     GCursor cb = ca;
     g_cur_next(cb, L);
     GCursor cc = cb;
     g_cur_next(cc, L);
-    uint64_t xa[4], xb[4], xc[4];
+    uint64_t xa[8], xb[8], xc[8];
     g_req_load(L, ca, q, xa);
     g_req_load(L, cb, q, xb);
     g_req_load(L, cc, q, xc);
@@ -683,14 +682,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
   } else if (warp == kGIssueWarp) {
     // ------------------------- MMA issue (one thread) -------------------------
     if (lane == 0) {
-      const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc_b(stage0 + 2 * kGTile);
+      const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc(stage0 + 2 * kGTileA);
+      const uint32_t sfa = tmem + kGSfa, sfb = tmem + kGSfb;
       uint32_t iter = 0, is = 0, iph = 0;  // stage count, slot, phase
       GWalk w = g_walk_start(L);
       for (uint32_t r = 0;; ++r) {
         GItem it;
         if (*abort_flag || !g_walk_next(L, w, it)) break;
         const uint32_t buf = L.nbuf == 2 ? (r & 1u) : 0u;
-        const uint32_t acc = tmem + buf * 256u;
+        const uint32_t acc = tmem + buf * kGCols;
         bool ok = true;
         if (r >= L.nbuf)
           ok = mb::wait_sleep(&acce[buf], ((r / L.nbuf) - 1u) & 1u, abort_flag, status, kGWaitNs, 64);
@@ -712,26 +712,22 @@ __global__ void __launch_bounds__(kGThreads, 1)
             iph ^= 1u;
           }
           const bool more = ks + kGKStage < it.k1;
-          // descriptors: the stage's bases plus constant K-step offsets (a
-          // single issuing thread is latency-bound: building descriptors
-          // from addresses before every MMA halved the tensor pipe's rate)
           const uint64_t sa = adesc0 + s * kDescStage, sb = bdesc0 + s * kDescStage;
           const uint32_t acc0 = ks > it.k0 ? 1u : 0u;
           const uint64_t left = it.k1 - ks;
-          const uint32_t nk = left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
+          const uint32_t nk =
+              left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
           const uint32_t total = nk * it.mt;  // MMAs of the stage: (K-step, tile) pairs
           if (total == 8) {
 #pragma unroll
             for (uint32_t q = 0; q < 7; ++q)
-              g_mma(acc + 256u * (q & 1u), sa + kDescTile * (q & 1u) + kDescKa * (q >> 1),
-                    sb + kDescKb * (q >> 1), (q >> 1) ? 1u : acc0);
-          } else if (total == 4 && it.mt == 1) {
-#pragma unroll
-            for (uint32_t q = 0; q < 3; ++q) g_mma(acc, sa + kDescKa * q, sb + kDescKb * q, q ? 1u : acc0);
+              g_mma(acc + kGCols * (q & 1u), sa + kDescTile * (q & 1u) + kDescK * (q >> 1),
+                    sb + kDescK * (q >> 1), sfa, sfb, (q >> 1) ? 1u : acc0);
           } else {
             for (uint32_t q = 0; q + 1 < total; ++q) {
               const uint32_t j = q / it.mt, t = q % it.mt;
-              g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+              g_mma(acc + kGCols * t, sa + kDescTile * t + kDescK * j, sb + kDescK * j, sfa, sfb,
+                    j ? 1u : acc0);
             }
           }
           bool next_ok = true;
@@ -741,7 +737,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
           }
           {
             const uint32_t q = total - 1, j = q / it.mt, t = q % it.mt;
-            g_mma(acc + 256u * t, sa + kDescTile * t + kDescKa * j, sb + kDescKb * j, j ? 1u : acc0);
+            g_mma(acc + kGCols * t, sa + kDescTile * t + kDescK * j, sb + kDescK * j, sfa, sfb,
+                  j ? 1u : acc0);
           }
           g_commit(&empty[s]);
           if (!more) break;
@@ -764,12 +761,12 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
       }
     }
-  } else if (warp >= 8 && warp < 16) {
+  } else if (warp >= kGEpiWarp0 && warp < kGEpiWarp0 + 8) {
     // ------------------------------ epilogue ------------------------------
     // Warp w reads tensor-memory lanes 32 (w % 4) .. + 31; the two groups of
-    // four warps take one M-tile each, or one half of the strip's words when
-    // the item has a single M-tile.
-    const uint32_t quarter = warp & 3u, half = (warp - 8) >> 2;
+    // four warps take one M-tile each, or four / three of the strip's seven
+    // words when the item has a single M-tile.
+    const uint32_t quarter = warp & 3u, half = (warp - kGEpiWarp0) >> 2;
     bool pdl_waited = false;
     GWalk w = g_walk_start(L);
     for (uint32_t e = 0;; ++e) {
@@ -785,11 +782,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
       const GJob& J = L.jobs[it.job];
       const uint32_t lanes = (32u * quarter) << 16;
       if (it.mt == 2) {
-        g_epilogue<kGWords>(J, tmem + lanes + 256u * half, it.b0 + 128u * half + 32u * quarter + lane,
-                            it.strip * kGWords);
+        g_epilogue(J, tmem + lanes + kGCols * half, it.b0 + 128u * half + 32u * quarter + lane,
+                   it.strip * kGStripWords, kGStripWords);
       } else {
-        g_epilogue<kGWords / 2>(J, tmem + lanes + buf * 256u + 32u * (kGWords / 2) * half,
-                                it.b0 + 32u * quarter + lane, it.strip * kGWords + (kGWords / 2) * half);
+        g_epilogue(J, tmem + lanes + buf * kGCols + 128u * half, it.b0 + 32u * quarter + lane,
+                   it.strip * kGStripWords + 4u * half, half ? kGStripWords - 4u : 4u);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mb::arrive(&acce[buf]);
@@ -799,39 +796,49 @@ __global__ void __launch_bounds__(kGThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 8)
+  if (warp == kGEpiWarp0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kGTmemCols)
                  : "memory");
 }
 
-// Tensor map of a table as a 2-D array of 32-bit words (Wd x n), box 8 words
-// x 128 rows; encoded once per (table, shape) through the driver entry point.
-cudaError_t g_table_map(const uint32_t* T, uint64_t n, uint32_t Wd, CUtensorMap* out) {
+PFN_cuTensorMapEncodeTiled_v12000 g_encoder() {
   static std::mutex mu;
-  static std::map<std::tuple<const void*, uint64_t, uint32_t>, CUtensorMap> cache;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   std::lock_guard<std::mutex> g(mu);
-  const auto key = std::make_tuple(static_cast<const void*>(T), n, Wd);
-  const auto it = cache.find(key);
-  if (it != cache.end()) {
-    *out = it->second;
-    return cudaSuccess;
-  }
   if (!encode) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q{};
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                      cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  return encode;
+}
+
+// Tensor map of a transposed table as a 2-D array of 64-bit words (row_bits
+// columns x ceil(n / 64) blocks), box 224 columns x 4 blocks; encoded once
+// per (copy, shape).
+cudaError_t g_table_map(const uint64_t* Tt, uint64_t n, uint32_t Wd, CUtensorMap* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, uint64_t, uint32_t>, CUtensorMap> cache;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = g_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple(static_cast<const void*>(Tt), n, Wd);
+  const auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return cudaSuccess;
   }
   CUtensorMap m;
-  const cuuint64_t dims[2] = {Wd, n};
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(Wd) * 4};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kGWords), 128};
+  const uint64_t row_bits = static_cast<uint64_t>(Wd) * 32;
+  const cuuint64_t dims[2] = {row_bits, (n + 63) / 64};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(row_bits) * 8};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kGCols), static_cast<cuuint32_t>(kGStageWords)};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(T), dims,
+  const CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(Tt), dims,
                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -846,19 +853,8 @@ cudaError_t g_table_map(const uint32_t* T, uint64_t n, uint32_t Wd, CUtensorMap*
 // rows stride_words apart, box bx words x by rows (zero fill outside).
 cudaError_t g_req_map(const uint64_t* R, uint64_t x, uint64_t y, uint64_t stride_words, uint32_t bx,
                       uint32_t by, CUtensorMap* out) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  static std::mutex mu;
-  {
-    std::lock_guard<std::mutex> g(mu);
-    if (!encode) {
-      void* fn = nullptr;
-      cudaDriverEntryPointQueryResult q{};
-      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                       cudaEnableDefault, &q);
-      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
-  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = g_encoder();
+  if (!encode) return cudaErrorNotSupported;
   const cuuint64_t dims[2] = {x, y};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(stride_words) * 8};
   const cuuint32_t box[2] = {bx, by};
@@ -894,7 +890,7 @@ GJob g_job(const uint64_t* R, uint32_t words64, uint32_t B, uint32_t* out, const
   j.Wd = Wd;
   j.words64 = words64;
   j.B = B;
-  j.n_strips = (Wd + kGWords - 1) / kGWords;
+  j.n_strips = (Wd + kGStripWords - 1) / kGStripWords;
   j.n_mb = (B + 255) / 256;
   j.stages = static_cast<uint32_t>((n + kGKStage - 1) / kGKStage);
   return j;
@@ -902,13 +898,14 @@ GJob g_job(const uint64_t* R, uint32_t words64, uint32_t B, uint32_t* out, const
 
 // How TMA can stage a job's request words (0: it cannot, per-thread loads).
 // TMA boxes start 16-byte aligned: the x coordinate of a stage's first word
-// is even, so with R 16-byte aligned rows of an even number of words are
-// staged as rows (1: box 2 words x min(B, 256) rows at (word, request));
-// rows of an odd number of words as row pairs, 16-byte aligned (2): the even
-// rows' two words (x = word, pair rows of 2 words64 words, dims nw x
-// ceil(B/2)), the odd rows' from the even word before theirs (x = words64 +
-// word - 1 in the pair, box 4 words, dims words64 + nw x floor(B/2)), where
-// nw = ceil(n/64) are the job's own words of a row: no box reads past them.
+// is a multiple of 4, so with R 16-byte aligned rows of an even number of
+// words are staged as rows (1: box 4 words x min(B, 256) rows at (word,
+// request)); rows of an odd number of words as row pairs, 16-byte aligned
+// (2): the even rows' four words (x = word, pair rows of 2 words64 words, dims
+// nw x ceil(B/2)), the odd rows' from the even word before theirs (x =
+// words64 + word - 1 in the pair, box 6 words, dims words64 + nw x
+// floor(B/2)), where nw = ceil(n/64) are the job's own words of a row: no box
+// reads past them.
 uint32_t g_req_mode(const uint64_t* R, uint32_t words64) {
   if (reinterpret_cast<uintptr_t>(R) & 15u) return 0;
   return (words64 & 1u) ? 2u : 1u;
@@ -916,21 +913,20 @@ uint32_t g_req_mode(const uint64_t* R, uint32_t words64) {
 void g_set_req(GJob& j, CUtensorMap* rmap, CUtensorMap* rmap_o) {
   j.req_tma = 0;
   const uint32_t mode = g_req_mode(j.R, j.words64);
-  // the job's own words of each row: ceil(n / 64) (a row shard's rows, words64
-  // apart, go on with other shards' words); boxes read zeros past them
   const uint64_t nw = (j.n + 63) / 64;
   if (mode == 1) {
-    if (g_req_map(j.R, nw, j.B, j.words64, 2, std::min<uint32_t>(j.B, 256), rmap) != cudaSuccess)
+    if (g_req_map(j.R, nw, j.B, j.words64, kGStageWords, std::min<uint32_t>(j.B, 256), rmap) !=
+        cudaSuccess)
       return;
     j.req_box = std::min<uint32_t>(j.B, 256);
     j.req_box_o = 0;
   } else if (mode == 2) {
     const uint32_t ev = (j.B + 1) / 2, od = j.B / 2;
-    if (g_req_map(j.R, nw, ev, 2ull * j.words64, 2, std::min<uint32_t>(ev, 128), rmap) !=
+    if (g_req_map(j.R, nw, ev, 2ull * j.words64, kGStageWords, std::min<uint32_t>(ev, 128), rmap) !=
         cudaSuccess)
       return;
-    if (od && g_req_map(j.R, j.words64 + nw, od, 2ull * j.words64, 4, std::min<uint32_t>(od, 128),
-                        rmap_o) != cudaSuccess)
+    if (od && g_req_map(j.R, j.words64 + nw, od, 2ull * j.words64, kGStageWords + 2,
+                        std::min<uint32_t>(od, 128), rmap_o) != cudaSuccess)
       return;
     j.req_box = std::min<uint32_t>(ev, 128);
     j.req_box_o = std::min<uint32_t>(od, 128);
@@ -941,8 +937,7 @@ void g_set_req(GJob& j, CUtensorMap* rmap, CUtensorMap* rmap_o) {
 }
 
 // k-chunks of kc_rows buckets: a multiple of a stage, at most kGMaxCount (a
-// k-chunk's counts stay in the range in which the fp32 accumulators were
-// checked exact, whatever the tensor cores' internal accumulation width)
+// k-chunk's counts stay within the range the fp32 accumulators hold exactly)
 uint32_t g_clamp_rows(uint64_t rows, uint64_t n) {
   rows = std::max<uint64_t>(rows, kGKStage);
   rows = (rows + kGKStage - 1) / kGKStage * kGKStage;
@@ -974,7 +969,7 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
+cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uint64_t* R,
                            uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                            cudaStream_t st) {
   if (B == 0) return cudaSuccess;
@@ -988,11 +983,7 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
   const uint64_t per_cta = (units + grid - 1) / grid;
   if (per_cta <= kGMaxCount / kGKStage) {
     // span mode: equal runs of stages per CTA, strip-major; partial strips of
-    // several CTAs XOR-reduce into replies initialised first.  (Ordering the
-    // stages in blocks of about one span, so that the CTAs of a block read
-    // the same rows together, cut DRAM reads of the paper-scale launch from
-    // 3x to 1.04x the table but took 7 % longer: the tail block's CTAs run
-    // several short items, and DRAM is not the bound here.)
+    // several CTAs XOR-reduce into replies initialised first
     L.span = 1;
     L.units = units;
     J.kc_rows = static_cast<uint32_t>(kGMaxCount);
@@ -1001,11 +992,11 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
   } else {
     // item mode (long spans): items of whole k-chunks, taken round by round
     // so that the CTAs of a round read the same rows; k-chunks minimise
-    // rounds x item time on the grid, item time ~ MMAs (128 cycles each at
-    // N = 256, K = 32) + epilogue, which the second accumulator hides when
-    // an item holds one M-tile
+    // rounds x item time on the grid, item time ~ MMAs (about 122 cycles
+    // each) + epilogue, which the second accumulator hides when an item
+    // holds one M-tile
     const double mts = B <= 128 ? 1.0 : 2.0;
-    const double epi = L.nbuf == 2 ? 600.0 : 2500.0;
+    const double epi = L.nbuf == 2 ? 600.0 : 3000.0;
     const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
     const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
     double best = 1e300;
@@ -1017,7 +1008,7 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
       const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
       const uint64_t rounds = (items + grid - 1) / grid;
       const double cost = static_cast<double>(rounds) *
-                          (static_cast<double>(rows) / kGKStep * mts * 128.0 + epi);
+                          (static_cast<double>(rows) / kGKStep * mts * 122.0 + epi);
       if (cost < best) {
         best = cost;
         best_rows = rows;
@@ -1033,7 +1024,7 @@ cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uin
   J.item_begin = 0;
   g_set_req(J, &L.rmaps[0], &L.rmaps_o[0]);
   L.jobs[0] = J;
-  cudaError_t e = g_table_map(T, n, Wd, &L.maps[0]);
+  cudaError_t e = g_table_map(Tt, n, Wd, &L.maps[0]);
   if (e != cudaSuccess) return e;
   if (J.req_tma == 1) return g_launch<1, 1>(L, st);
   if (J.req_tma == 2) return g_launch<1, 2>(L, st);
@@ -1055,6 +1046,7 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode,
   for (uint32_t i = 0; i < count; ++i) {
     const M4Request& q = reqs[i];
     if (q.B == 0) continue;
+    if (!q.Tt) return cudaErrorInvalidValue;
     GJob j = g_job(q.R, q.words64, q.B, q.out, q.seeds, q.n, q.Wd);
     all_small &= q.B <= 128;
     total += static_cast<double>(j.n_strips) * static_cast<double>(q.n) *
@@ -1068,7 +1060,8 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode,
   for (size_t i = 0; i < js.size(); ++i) {
     GJob& j = js[i];
     const double mt = j.B > 128 ? 2.0 : 1.0;
-    j.kc_rows = g_clamp_rows(static_cast<uint64_t>(target / mt), j.n);
+    j.kc_rows = src[i]->kc_rows ? g_clamp_rows(src[i]->kc_rows, j.n)
+                                : g_clamp_rows(static_cast<uint64_t>(target / mt), j.n);
     const uint64_t kcs = (j.n + j.kc_rows - 1) / j.kc_rows;
     j.split = (kcs > 1 || j.seeds) ? 1u : 0u;
     cost[i] = static_cast<double>(std::min<uint64_t>(j.kc_rows, j.n)) * mt;
@@ -1086,7 +1079,7 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode,
     j.item_begin = static_cast<uint32_t>(items);
     items += static_cast<uint64_t>(j.n_strips) * j.n_mb * kcs;
     if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
-    cudaError_t e = g_table_map(src[oi]->T, j.n, j.Wd, &L.maps[L.njobs]);
+    cudaError_t e = g_table_map(src[oi]->Tt, j.n, j.Wd, &L.maps[L.njobs]);
     if (e != cudaSuccess) return e;
     if (mode) {
       g_set_req(j, &L.rmaps[L.njobs], &L.rmaps_o[L.njobs]);

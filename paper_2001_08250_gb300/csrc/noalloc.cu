@@ -123,6 +123,9 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
                                                   static_cast<uint8_t*>(tmp));
     e = cudaGetLastError();
   }
+  // the tensor-core read's transposed copy (if the db has one) follows the
+  // moves; it allocates nothing
+  if (e == cudaSuccess) e = tcopy_after_moves(db, ops.data(), ops.size(), st);
   if (e == cudaSuccess) e = cudaEventRecord(db->last_write, st);
   if (e != cudaSuccess) {
     // the host placement is taken back: the table and its metadata agree

@@ -109,6 +109,7 @@ struct tpir_server {
   int device = 0;
   std::deque<Table> tables;  // stable addresses while tables are added
   uint64_t hbm_tables = 0;
+  uint64_t hbm_tcopies = 0;  // bit-transposed copies made for tensor-core reads
   uint64_t staging_reserve = 0;
   cudaStream_t streams[kServeStreams] = {nullptr};
 
@@ -327,9 +328,20 @@ bool form_unit(tpir_server* s, int si, int64_t* next_ready_ns) {
                                  static_cast<uint64_t>(b) * db->row_bytes, db->epoch});
     }
     if (!reads.empty()) {
+      // the tensor-core kernel reads a bit-transposed copy of the table (as
+      // large as the table), made on first use: only if it fits the budget
+      int choice = 0;
+      if (auto_kernel(db, B) == 5 && !db->d_tt) {
+        const uint64_t tt = tcopy_bytes(db->n, db->row_bytes);
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->hbm_tables + s->hbm_tcopies + tt + s->staging_reserve <= s->cfg.hbm_budget_bytes)
+          s->hbm_tcopies += tt;
+        else
+          choice = 2;
+      }
       int kernel = 0;
       cudaMemcpyAsync(sl.d_req, sl.h_req, req_bytes, cudaMemcpyHostToDevice, st);
-      const tpir_status r = enqueue_read(db, sl.d_req, B, sl.d_out, st, nullptr, &kernel);
+      const tpir_status r = enqueue_read(db, sl.d_req, B, sl.d_out, st, nullptr, &kernel, choice);
       cudaMemcpyAsync(sl.h_out, sl.d_out, out_bytes, cudaMemcpyDeviceToHost, st);
       std::lock_guard<std::mutex> g(s->cmu);
       s->launches++;
@@ -434,7 +446,8 @@ tpir_status tpir_serve_add_table(tpir_server* s, uint64_t n, uint32_t d, uint32_
   const uint64_t bytes = n * static_cast<uint64_t>(d) * msg_bytes;
   std::lock_guard<std::mutex> g(s->mu);
   if (s->stop) return TPIR_ESHUTDOWN;
-  if (s->hbm_tables + bytes + s->staging_reserve > s->cfg.hbm_budget_bytes) return TPIR_ENOMEM;
+  if (s->hbm_tables + s->hbm_tcopies + bytes + s->staging_reserve > s->cfg.hbm_budget_bytes)
+    return TPIR_ENOMEM;
   tpir_db* db = tpir_db_create(n, d, msg_bytes);
   if (!db) return tpir_last_error();
   s->tables.emplace_back();
@@ -566,7 +579,7 @@ tpir_status tpir_serve_stats(tpir_server* s, tpir_stats* st) {
   }
   {
     std::lock_guard<std::mutex> g(s->mu);
-    st->hbm_bytes_in_use = s->hbm_tables;
+    st->hbm_bytes_in_use = s->hbm_tables + s->hbm_tcopies;
   }
   for (const Slot& sl : s->slots) st->hbm_bytes_in_use += sl.d_req_cap + sl.d_out_cap;
   return TPIR_OK;

@@ -121,8 +121,9 @@ cudaError_t launch_zero_outputs(const ScanLaunch& L, cudaStream_t st);
 cudaError_t launch_init_replies(uint4* out, uint32_t B, uint32_t row_u4, const uint8_t* seeds,
                                 cudaStream_t st);
 // Tensor-core batched read (gf2mma.cu): the GF(2) product as an exact integer
-// product of 0/1 matrices on tcgen05, reduced mod 2.
-cudaError_t launch_gf2_mma(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
+// product of 0/1 matrices on tcgen05 (packed e2m1 operands), reduced mod 2.
+// Tt is the table's bit-transposed copy (tcopy.cu).
+cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uint64_t* R,
                            uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                            cudaStream_t st);
 struct M4Request;
@@ -161,6 +162,16 @@ cudaError_t launch_bloom_or(uint64_t* delta, const uint64_t* vec, uint64_t m, cu
 cudaError_t launch_bloom_union(const uint64_t* deltas, uint32_t window, uint64_t words,
                                uint64_t* out, cudaStream_t st);
 
+// Bit-transposed copy of a table for the tensor-core read (tcopy.cu):
+// Tt[kb][c] holds bit c of the rows of buckets 64 kb .. 64 kb + 63.
+constexpr uint32_t kTcopyMaxBlocks = 480;  // blocks a partial rebuild takes by value
+struct TcopyBlocks {
+  uint32_t count;  // 0: every block
+  uint32_t pad;
+  uint64_t kb[kTcopyMaxBlocks];
+};
+static_assert(sizeof(TcopyBlocks) + 64 < 32000, "kernel parameters must stay below 32 KB");
+uint64_t tcopy_bytes(uint64_t n, uint32_t row_bytes);
 int read_device_status_and_clear(int* status);
 // Device address of the status word on the current device (for kernels in
 // other translation units).
@@ -175,6 +186,8 @@ struct M4Request {
   uint32_t B;
   uint32_t* out;
   const uint8_t* seeds;  // B x 32-byte mask seeds, or null
+  const uint64_t* Tt = nullptr;  // tensor-core jobs: the bit-transposed table
+  uint32_t kc_rows = 0;          // tensor-core jobs: k-chunk rows (0: planned)
 };
 cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
                         uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
@@ -315,18 +328,31 @@ struct tpir_db {
   uint64_t pipe_cap = 0;
   cudaEvent_t pipe_ev[9] = {nullptr};
   tpir_bloom_state bloom;
+  // bit-transposed copy for the tensor-core read (allocated on first use,
+  // then kept equal to the table in stream order)
+  uint64_t* d_tt = nullptr;
+  bool tt_valid = false;
 };
 
 namespace tpir {
+// The bit-transposed copy (tcopy.cu): built if missing or stale, rebuilt after
+// a bulk load (if it exists), and its blocks holding moved slots rebuilt after
+// a write's moves; each enqueued on `st` after the table's own update.
+cudaError_t tcopy_ensure(tpir_db* db, cudaStream_t st);
+cudaError_t tcopy_after_load(tpir_db* db, cudaStream_t st);
+cudaError_t tcopy_after_moves(tpir_db* db, const MoveOp* ops, size_t nops, cudaStream_t st);
 tpir_status set_error(tpir_status s);
 tpir_status cuda_status(cudaError_t e);
 // enqueue a read of db on stream (device buffers), honoring write ordering;
 // d_seeds (B x 32 bytes) masks the replies (serialized PIR), null = plain
 // (*kernel_used, if given, receives the kernel chosen: 1 plain, 2 register-
 // tiled, 3 plain register-streaming, 4 Four-Russians, 5 tensor-core)
+// kernel_choice (0 = automatic) overrides the choice
 tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d_out,
                          cudaStream_t st, const uint8_t* d_seeds = nullptr,
-                         int* kernel_used = nullptr);
+                         int* kernel_used = nullptr, int kernel_choice = 0);
+// The kernel a read of B requests takes on db unless told otherwise.
+int auto_kernel(const tpir_db* db, uint32_t B);
 // order stream `st` after the db's last write, and record a read event
 void order_after_writes(tpir_db* db, cudaStream_t st);
 void note_read(tpir_db* db, cudaStream_t st);
@@ -342,6 +368,7 @@ tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, 
 // batches, register-tiled for the rest); no cross-stream ordering done here.
 tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st);
 tpir_status enqueue_multi_lop3(const tpir_read_job* jobs, uint32_t njobs, cudaStream_t st);
+int multi_kernel(const tpir_read_job& q);
 void order_writes_after_reads(tpir_db* db, cudaStream_t st);
 bool grow_dev(void** p, uint64_t* cap, uint64_t need);
 bool grow_pinned(void** p, uint64_t* cap, uint64_t need);

@@ -47,6 +47,53 @@ def test_write_batches_match_oracle(n, d, z, cap, maxev, seed, batches):
     assert talekpir.device_status() == talekpir.OK
 
 
+def test_tensor_reads_follow_writes_and_loads():
+    """The tensor-core read uses a bit-transposed copy of the table, which
+    every write (single writes with their moves in the launch, staged
+    batches, the no-alloc write) and every bulk load must keep current: after
+    each of them a forced tensor-core read of 100 requests equals the oracle's
+    replies on the table at that point."""
+    import ctypes
+    torch = require_cuda()
+    n, d, z, cap, seed = 3000, 2, 256, 5400, 71
+    b1, b2, M = _writes(2600, n, z, seed)
+    oc = oracle.Cuckoo(n, d, z, cap, 500, seed=seed)
+    db = talekpir.DB(n, d, z)
+    db.set_policy(cap, 500, seed)
+    db.set_kernel(5)
+    R = synth.random_bits(100, n, seed=seed + 1)
+
+    def check(what):
+        assert np.array_equal(db.read_batch(R), oracle.read_batch(oc.table(), n, d, z, R)), what
+
+    check("empty table")            # builds the copy
+    i = 0
+    for count in (1, 1, 7, 300, 1, 900):   # parameter-passed moves and staged batches
+        if count == 1:
+            rc, _ = db.write(int(b1[i]), int(b2[i]), M[i])
+            assert rc == oc.insert(int(b1[i]), int(b2[i]), M[i])[0]
+        else:
+            st, _ = db.write_batch(b1[i:i + count], b2[i:i + count], M[i:i + count])
+            for j in range(count):
+                assert st[j] == oc.insert(int(b1[i + j]), int(b2[i + j]), M[i + j])[0]
+        i += count
+        check(f"after {i} writes")
+    dM = torch.from_numpy(M[i:i + 50]).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    for j in range(50):
+        ev = ctypes.c_uint32(0)
+        rc = talekpir.lib().tpir_write_noalloc(db.h, int(b1[i + j]), int(b2[i + j]),
+                                               dM[j].data_ptr(), ctypes.byref(ev), stream)
+        assert rc == oc.insert(int(b1[i + j]), int(b2[i + j]), M[i + j])[0]
+    torch.cuda.synchronize()
+    check("after no-alloc writes")
+    T2 = synth.table_bytes(n, d, z, seed=seed + 2)
+    db.load(T2)
+    assert np.array_equal(db.read_batch(R), oracle.read_batch(T2, n, d, z, R)), "after a load"
+    db.close()
+    assert talekpir.device_status() == talekpir.OK
+
+
 def test_single_writes_and_rollback():
     require_cuda()
     n, d, z = 3, 1, 32
