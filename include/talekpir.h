@@ -228,22 +228,41 @@ tpir_status tpir_xor_combine(const void *const *d_srcs, uint32_t count, uint64_t
  * that uses it and then kept equal to the table by every write and load. */
 tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
 
-/* Autotuner of the batched kernel's tile shape: times every admissible shape
- * (lanes along the row, warps along requests / row / buckets, i.e. the batch
- * tile width and the row tile width, and the rows per pipeline stage) for
- * this table's row width and a batch of B requests, on the table itself, and
- * keeps the fastest for every later launch of that row width and batch-size
- * class (ceil(log2 B)).  reps = timed launches per shape (0 = 3).  Allocates
+/* Autotuner of the batched read.  For this table and a batch of B requests
+ * it times, on the table itself:
+ *   - every admissible tile shape of the register-tiled kernel (lanes along
+ *     the row, warps along requests / row / buckets, i.e. the batch tile
+ *     width and the row tile width, and the rows per pipeline stage);
+ *   - the tensor-core kernel's schedules (equal spans of stages per CTA, or
+ *     items of whole k-chunks of 4096 .. 32768 buckets or the planned size;
+ *     request words staged by TMA or loaded by the expander threads) when
+ *     rows are 256 bytes or wider;
+ *   - the Four-Russians kernel (B >= 32, rows of 256 bytes or more) and the
+ *     plain kernel (B <= 16);
+ * and keeps (a) the fastest tile shape for every later launch of the
+ * register-tiled kernel with this row width and batch-size class
+ * (ceil(log2 B)), and (b) the fastest kernel, with its tensor-core schedule,
+ * for every later automatic choice with this row width, batch class and
+ * table-size class (ceil(log2 n)): single-table reads, many-table launches
+ * and the serve loop then take the measured winner instead of the built-in
+ * batch thresholds.  reps = timed launches per candidate (0 = 3).  Allocates
  * scratch buffers for the trial requests and replies. */
 typedef struct {
     uint32_t lw_log2, warps_b, warps_w, warps_k, stage_rows;
     uint32_t tile_b, tile_w;   /* requests and 32-bit words per CTA tile */
-    uint32_t candidates;       /* shapes timed */
-    double us_per_launch;      /* of the chosen shape */
+    uint32_t candidates;       /* register-tiled shapes timed */
+    double us_per_launch;      /* of the chosen register-tiled shape */
     double lop3_tops;          /* B*n*row_words / time */
+    uint32_t kernel;           /* fastest kernel (as in tpir_db_set_kernel) */
+    uint32_t tensor_mode;      /* its tensor-core schedule: 1 spans, 2 items */
+    uint32_t tensor_kc_rows;   /* items: k-chunk buckets (0: planned size) */
+    uint32_t tensor_loads;     /* 1: request words loaded by threads, not TMA */
+    uint32_t tensor_candidates;
+    double us_lop3, us_tensor, us_m4rm, us_plain;  /* best of each kernel (0: not timed) */
 } tpir_tune_result;
 tpir_status tpir_autotune(tpir_db *db, uint32_t B, uint32_t reps, tpir_tune_result *out);
-/* The tuned shapes as JSON (one plan per line), and back; clear forgets them. */
+/* The tuned shapes and kernel choices as JSON (one plan per line), and back;
+ * clear forgets them. */
 tpir_status tpir_tune_save(const char *path);
 tpir_status tpir_tune_load(const char *path);
 tpir_status tpir_tune_clear(void);

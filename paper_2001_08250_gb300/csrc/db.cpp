@@ -11,7 +11,6 @@
 
 namespace {
 thread_local tpir_status g_last = TPIR_OK;
-constexpr uint32_t kPlainMaxB = 4;
 }  // namespace
 
 namespace tpir {
@@ -141,6 +140,8 @@ uint32_t next_counter_slot() {
 
 int auto_kernel(const tpir_db* db, uint32_t B) {
   if (db->forced_kernel) return db->forced_kernel;
+  KernelPlan kp;
+  if (kernel_plan_lookup(db->Wd, B, db->n, &kp)) return kp.kernel;  // measured winner
   // plain stream for a few requests; the tensor-core kernel once its
   // 128-request M-tiles are well filled (measured crossover with the
   // register-tiled kernel on GB300); the register-tiled kernel in between
@@ -170,10 +171,13 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
                        kernel == 3 ? -1 : 0);
     }
   } else if (kernel == 5) {
+    KernelPlan kp;
+    const bool planned = kernel_plan_lookup(db->Wd, B, db->n, &kp) && kp.kernel == 5;
     e = tcopy_ensure(db, st);
     if (e == cudaSuccess)
       e = launch_gf2_mma(db->d_tt, db->n, db->Wd, d_req, db->words64, B,
-                         reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
+                         reinterpret_cast<uint32_t*>(d_out), d_seeds, st,
+                         planned ? &kp.sched : nullptr);
   } else if (kernel == 4) {
     e = launch_m4rm(reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, d_req,
                     db->words64, B, reinterpret_cast<uint32_t*>(d_out), d_seeds, st);
@@ -315,7 +319,15 @@ tpir_status bloom_insert_core(tpir_db* db, const uint64_t* pos, uint32_t count, 
 int multi_kernel(const tpir_read_job& q) {
   const int forced = q.db->forced_kernel;
   if (forced == 4 && q.db->Wd >= 64) return 4;
-  if (forced == 5 || (forced == 0 && q.B >= kTensorMinB && q.db->Wd >= 64)) return 5;
+  if (forced == 5) return 5;
+  if (forced == 0) {
+    KernelPlan kp;
+    if (kernel_plan_lookup(q.db->Wd, q.B, q.db->n, &kp)) {
+      if (kp.kernel == 5 || (kp.kernel == 4 && q.db->Wd >= 64)) return kp.kernel;
+      return 2;  // the plain kernel's jobs run in the register-tiled launch
+    }
+    if (q.B >= kTensorMinB && q.db->Wd >= 64) return 5;
+  }
   return 2;
 }
 
@@ -345,6 +357,11 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
       if (e != cudaSuccess) return cuda_status(e);
       M4Request t = r;
       t.Tt = q.db->d_tt;
+      KernelPlan kp;
+      if (kernel_plan_lookup(q.db->Wd, q.B, q.db->n, &kp) && kp.kernel == 5) {
+        if (kp.sched.mode == 2) t.kc_rows = kp.sched.kc_rows;
+        t.loads = kp.sched.loads;
+      }
       tc.push_back(t);
     } else {
       lop3.push_back(q);

@@ -23,8 +23,8 @@
 // columns (two M-tiles of one item, or one M-tile of two items
 // double-buffered) and the scale factors in columns 448..511.
 //
-// Data flow per CTA (persistent, one per SM, 672 threads):
-//   warp 11     streams, by 2-D TMA, each stage's 4 words of the strip's 224
+// Data flow per CTA (persistent, one per SM, 800 threads):
+//   warp 15     streams, by 2-D TMA, each stage's 4 words of the strip's 224
 //               columns of the transposed table and the stage's 4 words of
 //               the item's requests into a ring of raw stages: rows of an
 //               even number of 64-bit words as rows, of an odd number as row
@@ -32,11 +32,11 @@
 //               a request buffer that is not 16-byte aligned;
 //   warps 0-6   table expanders: lane = column; its 256 bits of the stage
 //               become 128 bytes of e2m1 (the column's row of the B operand);
-//   warps 7-10  request expanders: lane = two requests (q, 128 + q); their
-//               256 bits each become the A operand rows;
-//   warp 20     one thread issues the MMAs of each stage and commits them to
+//   warps 7-14  request expanders: lane = request q of the item's (up to)
+//               256; its 256 bits of the stage become its A operand row;
+//   warp 24     one thread issues the MMAs of each stage and commits them to
 //               the stage's "empty" barrier;
-//   warps 12-19 epilogue: read the accumulators (tcgen05.ld), take each sum's
+//   warps 16-23 epilogue: read the accumulators (tcgen05.ld), take each sum's
 //               parity, and store (single k-chunk) or XOR-reduce (split, or a
 //               masked read) the reply words; two groups of four warps split
 //               an item (one M-tile, or four / three of its seven words).
@@ -78,15 +78,16 @@ constexpr int kGStageBytes = 2 * kGTileA + kGTileB;
 // (k / 16) kGLbo + (r % 8) 16.
 constexpr int kGLbo = 128;
 constexpr int kGSbo = (kGRowBytes / 16) * 128;
-constexpr uint32_t kGTableWarps = 7, kGReqWarp0 = 7, kGReqWarps = 4;
-constexpr uint32_t kGTmaWarp = 11, kGEpiWarp0 = 12, kGIssueWarp = 20;
-constexpr int kGThreads = 21 * 32;
+constexpr uint32_t kGTableWarps = 7, kGReqWarp0 = 7, kGReqWarps = 8;
+constexpr uint32_t kGTmaWarp = 15, kGEpiWarp0 = 16, kGIssueWarp = 24;
+constexpr int kGThreads = 25 * 32;
 constexpr int kGRawTable = kGCols * kGStageWords * 8;  // 4 words of 224 columns: 7 KiB
 // Raw stages (table words + request words) by request-staging mode RM:
 // RM = 1: 256 request rows x 32 bytes; RM = 2 (rows of an odd number of
 // words, staged as row pairs): 128 even rows x 32 bytes, then 128 odd rows x
 // 48 bytes (a 6-word box from the even word before the stage's four); RM = 0:
-// the table words only (requests loaded by the expanders).
+// the table words only (requests loaded by the expanders), so twice as many
+// stages fit.
 template <int RM>
 __host__ __device__ constexpr int g_raw_req() { return RM == 1 ? 256 * 32 : RM == 2 ? 128 * 32 + 128 * 48 : 0; }
 template <int RM>
@@ -309,28 +310,25 @@ __device__ __forceinline__ void g_tma_load(uint32_t dst, const CUtensorMap* map,
       : "memory");
 }
 
-// the request words of one stage for this thread's request in each M-tile
+// the request words of one stage for this thread's request q of the item
 // (zeros past the job's words and the batch), loaded from global memory
 template <int NJ>
 __device__ __forceinline__ void g_req_load(const GLaunch<NJ>& L, const GCursor& c, uint32_t q,
-                                           uint64_t (&x)[8]) {
+                                           uint64_t (&x)[kGStageWords]) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) x[i] = 0ull;
+  for (int i = 0; i < kGStageWords; ++i) x[i] = 0ull;
   if (!c.valid) return;
   const GJob& J = L.jobs[c.it.job];
   const uint64_t wi = c.ks >> 6;
   // the job's own words end at ceil(n / 64): a row shard's request rows are
   // longer (words64 is the stride) and go on with other shards' words
   const uint64_t nw = (J.n + 63) / 64;
+  const uint32_t b = c.it.b0 + q;
+  if ((q >> 7) < c.it.mt && b < J.B) {
+    const uint64_t* rq = J.R + static_cast<uint64_t>(b) * J.words64;
 #pragma unroll
-  for (uint32_t t = 0; t < 2; ++t) {
-    const uint32_t b = c.it.b0 + 128u * t + q;
-    if (t < c.it.mt && b < J.B) {
-      const uint64_t* rq = J.R + static_cast<uint64_t>(b) * J.words64;
-#pragma unroll
-      for (uint32_t i = 0; i < kGStageWords; ++i)
-        if (wi + i < nw) x[4 * t + i] = __ldg(rq + wi + i);
-    }
+    for (uint32_t i = 0; i < kGStageWords; ++i)
+      if (wi + i < nw) x[i] = __ldg(rq + wi + i);
   }
 }
 
@@ -401,28 +399,25 @@ __device__ __forceinline__ void g_epilogue(const GJob& J, uint32_t taddr, uint32
   }
 }
 
-// The request operand of one stage: this thread's request in each M-tile
-// (the stage's 256 bits as e2m1, K-major), written once the stage slot is
-// free, then this warp's arrival on the stage's "full" barrier.  False if
-// the CTA aborted.
+// The request operand of one stage: this thread's request q of the item
+// (row q % 128 of M-tile q / 128; the stage's 256 bits as e2m1, K-major),
+// written once the stage slot is free, then this warp's arrival on the
+// stage's "full" barrier.  False if the CTA aborted.
 template <int NJ>
 __device__ __forceinline__ bool g_req_stage(const GLaunch<NJ>& L, const GCursor& c,
-                                            const uint64_t (&x)[8], uint32_t iter, uint32_t q,
-                                            uint32_t lane, uint32_t stage0, uint64_t* full,
-                                            uint64_t* empty, volatile int* abort_flag, int* status) {
+                                            const uint64_t (&x)[kGStageWords], uint32_t iter,
+                                            uint32_t q, uint32_t lane, uint32_t stage0,
+                                            uint64_t* full, uint64_t* empty,
+                                            volatile int* abort_flag, int* status) {
   const uint32_t s = iter % kGStages, ph = (iter / kGStages) & 1u;
   if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) return false;
-  const uint32_t st = stage0 + s * kGStageBytes;
+  const uint32_t t = q >> 7, b = c.it.b0 + q;
+  if (t < c.it.mt && b < L.jobs[c.it.job].B) {
+    const uint32_t o = stage0 + s * kGStageBytes + t * kGTileA + g_off(q & 127u, 0);
 #pragma unroll
-  for (uint32_t t = 0; t < 2; ++t) {
-    const uint32_t b = c.it.b0 + 128u * t + q;
-    if (t < c.it.mt && b < L.jobs[c.it.job].B) {
-      const uint32_t o = st + t * kGTileA + g_off(q, 0);
-#pragma unroll
-      for (uint32_t i = 0; i < kGStageWords; ++i) {  // K-step i: buckets ks + 64 i ..
-        st_shared_v4(o + (2 * i) * kGLbo, g_spread(static_cast<uint32_t>(x[4 * t + i])));
-        st_shared_v4(o + (2 * i + 1) * kGLbo, g_spread(static_cast<uint32_t>(x[4 * t + i] >> 32)));
-      }
+    for (uint32_t i = 0; i < kGStageWords; ++i) {  // K-step i: buckets ks + 64 i ..
+      st_shared_v4(o + (2 * i) * kGLbo, g_spread(static_cast<uint32_t>(x[i])));
+      st_shared_v4(o + (2 * i + 1) * kGLbo, g_spread(static_cast<uint32_t>(x[i] >> 32)));
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -437,7 +432,7 @@ __device__ __forceinline__ bool g_req_stage(const GLaunch<NJ>& L, const GCursor&
 // if the CTA aborted.
 template <int NJ, int RM>
 __device__ __forceinline__ bool g_req_step(const GLaunch<NJ>& L, const GCursor& c,
-                                           const uint64_t (&x)[8], uint32_t iter, uint32_t q,
+                                           const uint64_t (&x)[kGStageWords], uint32_t iter, uint32_t q,
                                            uint32_t lane, uint32_t stage0, uint32_t raw0,
                                            uint64_t* full, uint64_t* empty, uint64_t* raw_full,
                                            uint64_t* raw_empty, volatile int* abort_flag,
@@ -449,30 +444,28 @@ __device__ __forceinline__ bool g_req_step(const GLaunch<NJ>& L, const GCursor& 
     const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
     if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) return false;
     const uint32_t base = raw0 + rs * kGRawBytes + kGRawTable;
-    uint64_t y[8];
+    uint64_t y[kGStageWords];
+    if constexpr (RM == 1) {
+      const uint32_t a = base + q * 32u;
+      const uint4 v0 = ld_shared_v4(a), v1 = ld_shared_v4(a + 16u);
+      y[0] = v0.x | static_cast<uint64_t>(v0.y) << 32;
+      y[1] = v0.z | static_cast<uint64_t>(v0.w) << 32;
+      y[2] = v1.x | static_cast<uint64_t>(v1.y) << 32;
+      y[3] = v1.z | static_cast<uint64_t>(v1.w) << 32;
+    } else {
+      // request q of the block: even rows' words at their pair's 32 bytes,
+      // odd rows' at bytes 8 .. 39 of their pair's 48
+      const uint32_t pr = q >> 1;
+      const uint32_t a = (q & 1u) ? base + 128u * 32u + pr * 48u + 8u : base + pr * 32u;
 #pragma unroll
-    for (uint32_t t = 0; t < 2; ++t) {
-      if constexpr (RM == 1) {
-        const uint32_t a = base + (128u * t + q) * 32u;
-        const uint4 v0 = ld_shared_v4(a), v1 = ld_shared_v4(a + 16u);
-        y[4 * t + 0] = v0.x | static_cast<uint64_t>(v0.y) << 32;
-        y[4 * t + 1] = v0.z | static_cast<uint64_t>(v0.w) << 32;
-        y[4 * t + 2] = v1.x | static_cast<uint64_t>(v1.y) << 32;
-        y[4 * t + 3] = v1.z | static_cast<uint64_t>(v1.w) << 32;
-      } else {
-        // request 128 t + q of the block: even rows' words at their pair's
-        // 32 bytes, odd rows' at bytes 8 .. 39 of their pair's 48
-        const uint32_t pr = 64u * t + (q >> 1);
-        const uint32_t a = (q & 1u) ? base + 128u * 32u + pr * 48u + 8u : base + pr * 32u;
-#pragma unroll
-        for (uint32_t i = 0; i < kGStageWords; ++i) y[4 * t + i] = ld_shared_u64(a + 8u * i);
-      }
+      for (uint32_t i = 0; i < kGStageWords; ++i) y[i] = ld_shared_u64(a + 8u * i);
     }
     // the words are in registers (the fence depends on them) and ordered
     // before the async proxy's next write to the slot, then the slot is free
     uint32_t used = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) used ^= static_cast<uint32_t>(y[i]) ^ static_cast<uint32_t>(y[i] >> 32);
+    for (int i = 0; i < kGStageWords; ++i)
+      used ^= static_cast<uint32_t>(y[i]) ^ static_cast<uint32_t>(y[i] >> 32);
     asm volatile("fence.proxy.async.shared::cta;" ::"r"(used) : "memory");
     __syncwarp();
     if (lane == 0) mb::arrive(&raw_empty[rs]);
@@ -632,26 +625,26 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
   } else if (warp < kGReqWarp0 + kGReqWarps && RM != 0) {
     // ------------------- request expanders (TMA-staged words) -------------------
-    // Thread q takes requests q and 128 + q of the item's (up to) 256.
+    // Thread q takes request q of the item's (up to) 256.
     const uint32_t q = threadIdx.x - 32u * kGReqWarp0;
     uint32_t iter = 0;
-    const uint64_t none[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint64_t none[kGStageWords] = {0, 0, 0, 0};
     for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter)
       if (!g_req_step<NJ, RM>(L, c, none, iter, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
                              abort_flag, status))
         break;
   } else if (warp < kGReqWarp0 + kGReqWarps) {
     // ------------------------ request expanders ------------------------
-    // Thread q takes requests q and 128 + q of the item's (up to) 256, loaded
-    // from global memory into three register sets, each loaded three stages
-    // ahead of its use so that a stage does not wait on their (L2) latency.
+    // Thread q takes request q of the item's (up to) 256, loaded from global
+    // memory into three register sets, each loaded three stages ahead of its
+    // use so that a stage does not wait on their (L2) latency.
     const uint32_t q = threadIdx.x - 32u * kGReqWarp0;
     GCursor ca = g_cur_start(L);
     GCursor cb = ca;
     g_cur_next(cb, L);
     GCursor cc = cb;
     g_cur_next(cc, L);
-    uint64_t xa[8], xb[8], xc[8];
+    uint64_t xa[kGStageWords], xb[kGStageWords], xc[kGStageWords];
     g_req_load(L, ca, q, xa);
     g_req_load(L, cb, q, xb);
     g_req_load(L, cc, q, xc);
@@ -969,9 +962,16 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
 
 }  // namespace
 
+bool gf2_span_ok(uint64_t n, uint32_t Wd, uint32_t B) {
+  const GJob J = g_job(nullptr, 0, B, nullptr, nullptr, n, Wd);
+  const uint64_t units = static_cast<uint64_t>(J.n_mb) * J.n_strips * J.stages;
+  const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(units, device_sm_count()));
+  return (units + grid - 1) / grid <= kGMaxCount / kGKStage;
+}
+
 cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uint64_t* R,
                            uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
-                           cudaStream_t st) {
+                           cudaStream_t st, const GSched* sched) {
   if (B == 0) return cudaSuccess;
   GLaunch<1> L{};
   L.njobs = 1;
@@ -981,7 +981,9 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
   if (units > (1ull << 48)) return cudaErrorInvalidValue;
   const uint64_t grid = std::min<uint64_t>(units, device_sm_count());
   const uint64_t per_cta = (units + grid - 1) / grid;
-  if (per_cta <= kGMaxCount / kGKStage) {
+  const uint32_t mode = sched ? sched->mode : 0u;
+  const bool span_ok = per_cta <= kGMaxCount / kGKStage;
+  if (span_ok && mode != 2) {
     // span mode: equal runs of stages per CTA, strip-major; partial strips of
     // several CTAs XOR-reduce into replies initialised first
     L.span = 1;
@@ -1015,6 +1017,7 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
       }
     }
     J.kc_rows = static_cast<uint32_t>(best_rows);
+    if (mode == 2 && sched->kc_rows) J.kc_rows = g_clamp_rows(sched->kc_rows, n);
     const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;
     const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
     if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
@@ -1022,7 +1025,7 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
     L.total_items = static_cast<uint32_t>(items);
   }
   J.item_begin = 0;
-  g_set_req(J, &L.rmaps[0], &L.rmaps_o[0]);
+  if (!(sched && sched->loads)) g_set_req(J, &L.rmaps[0], &L.rmaps_o[0]);
   L.jobs[0] = J;
   cudaError_t e = g_table_map(Tt, n, Wd, &L.maps[0]);
   if (e != cudaSuccess) return e;
@@ -1103,7 +1106,8 @@ cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStre
   for (uint32_t mode : {1u, 2u, 0u}) {
     std::vector<M4Request> part;
     for (uint32_t i = 0; i < count; ++i)
-      if (reqs[i].B && g_req_mode(reqs[i].R, reqs[i].words64) == mode) part.push_back(reqs[i]);
+      if (reqs[i].B && (reqs[i].loads ? 0u : g_req_mode(reqs[i].R, reqs[i].words64)) == mode)
+        part.push_back(reqs[i]);
     for (size_t i = 0; i < part.size(); i += kGMultiJobs) {
       const uint32_t c = static_cast<uint32_t>(std::min<size_t>(kGMultiJobs, part.size() - i));
       const cudaError_t e = g_launch_multi(part.data() + i, c, mode, st);

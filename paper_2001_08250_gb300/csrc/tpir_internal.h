@@ -82,12 +82,30 @@ static_assert(sizeof(ScanLaunch) <= 32000, "kernel parameters must stay below 32
 // Assigns the next item-counter slot (rotating).
 uint32_t next_counter_slot();
 
+// Schedule of a one-table tensor-core launch: mode 0 = planned (spans when
+// every CTA gets at most one k-chunk of stages, else items of k-chunks sized
+// by the cost model), 1 = spans (if admissible), 2 = items of kc_rows buckets
+// (0: the cost model's size); loads = 1: request words loaded by the
+// expander threads instead of staged by TMA (room for a deeper ring of table
+// stages).
+struct GSched {
+  uint32_t mode = 0;
+  uint32_t kc_rows = 0;
+  uint32_t loads = 0;
+};
 // Fills a job's tiling from its shape/k-chunking and validates smem fit.
 bool finalize_job(ScanJob& j);
 Shape choose_shape(uint32_t Wd, uint32_t B);
 // Tuned shapes (plan.cpp): the shape the autotuner measured fastest for a
 // row width and a batch-size class, if any.
 bool plan_lookup(uint32_t Wd, uint32_t B, Shape* out);
+// Tuned kernel choice (plan.cpp) for a row width, batch-size class and
+// table-size class: the kernel and, for the tensor-core kernel, its schedule.
+struct KernelPlan {
+  int kernel = 0;
+  GSched sched;
+};
+bool kernel_plan_lookup(uint32_t Wd, uint32_t B, uint64_t n, KernelPlan* out);
 int scan_stage_bytes(const Shape& s);
 
 // Launch with programmatic dependent launch (PDL) allowed: the kernel may
@@ -125,7 +143,10 @@ cudaError_t launch_init_replies(uint4* out, uint32_t B, uint32_t row_u4, const u
 // Tt is the table's bit-transposed copy (tcopy.cu).
 cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uint64_t* R,
                            uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
-                           cudaStream_t st);
+                           cudaStream_t st, const GSched* sched = nullptr);
+// True if span mode is admissible for this shape (at most one k-chunk of
+// stages per CTA).
+bool gf2_span_ok(uint64_t n, uint32_t Wd, uint32_t B);
 struct M4Request;
 // Many tables in one launch of the tensor-core kernel (up to TPIR_MAX_JOBS).
 cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st);
@@ -188,6 +209,7 @@ struct M4Request {
   const uint8_t* seeds;  // B x 32-byte mask seeds, or null
   const uint64_t* Tt = nullptr;  // tensor-core jobs: the bit-transposed table
   uint32_t kc_rows = 0;          // tensor-core jobs: k-chunk rows (0: planned)
+  uint32_t loads = 0;            // tensor-core jobs: request words loaded by threads
 };
 cudaError_t launch_m4rm(const uint32_t* T, uint64_t n, uint32_t Wd, const uint64_t* R,
                         uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
@@ -202,6 +224,7 @@ cudaError_t launch_xor_combine(const uint4* const* srcs, uint32_t count, uint64_
 // wide: 512-request tiles (jobs of more than 256 requests), else 256
 cudaError_t launch_m4rm_multi(const M4Request* reqs, uint32_t count, bool wide, cudaStream_t st);
 constexpr uint32_t kM4rmMinB = 176;  // batch from which the Four-Russians kernel beats LOP3
+constexpr uint32_t kPlainMaxB = 4;    // requests per launch of the plain kernel
 constexpr uint32_t kTensorMinB = 48;  // batch from which the tensor-core kernel beats LOP3 (measured)
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st);
 // Rice coding of sparse bit vectors (rice.cu).

@@ -44,7 +44,11 @@ class ServeConfig(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("lw_log2", _u32), ("warps_b", _u32), ("warps_w", _u32), ("warps_k", _u32),
                 ("stage_rows", _u32), ("tile_b", _u32), ("tile_w", _u32), ("candidates", _u32),
-                ("us_per_launch", ctypes.c_double), ("lop3_tops", ctypes.c_double)]
+                ("us_per_launch", ctypes.c_double), ("lop3_tops", ctypes.c_double),
+                ("kernel", _u32), ("tensor_mode", _u32), ("tensor_kc_rows", _u32),
+                ("tensor_loads", _u32), ("tensor_candidates", _u32), ("us_lop3", ctypes.c_double),
+                ("us_tensor", ctypes.c_double), ("us_m4rm", ctypes.c_double),
+                ("us_plain", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

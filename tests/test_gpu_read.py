@@ -291,6 +291,43 @@ def test_multi_table_large_batches_bit_exact():
     assert talekpir.device_status() == talekpir.OK
 
 
+@pytest.mark.parametrize("n,B,loads", [(32768, 128, 0), (32767, 256, 0), (65536, 200, 1),
+                                       (32768, 64, 1)])
+def test_tensor_kernel_counts_at_the_chunk_bound(n, B, loads, tmp_path):
+    """One accumulator over a whole k-chunk of 32 768 buckets: a tuning plan
+    (loaded as a user would) makes the tensor-core read take items of whole
+    32 768-bucket k-chunks, and all-ones requests then drive each count to
+    its largest values: 32 767 (odd: a column set on every row but one, or
+    every row of a 32 767-bucket table) and 32 768 (even), besides counts of
+    16 384 and 10 923 (rows k odd, rows k = 0 mod 3).  With 65 536 buckets two
+    full chunks are XOR-combined.  Every reply bit-exact."""
+    require_cuda()
+    d, z = 1, 256                       # 64 words: a row width plans may steer
+    T = np.zeros((n, d * z), dtype=np.uint8)
+    T[1:, 0:4] = 0xFF                   # every row but row 0
+    T[:, 4:8] = 0xFF                    # every row
+    T[1::2, 8:12] = 0xFF                # odd rows
+    T[0::3, 12:16] = 0xFF               # rows 0 mod 3
+    T[:, 16:] = synth.table_bytes(n, 1, 240, seed=95)
+    R = np.full((B, (n + 63) // 64), np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+    bclass = max(0, (B - 1).bit_length())
+    nclass = max(0, (n - 1).bit_length())
+    plan = tmp_path / "plan.json"
+    plan.write_text('{"plans": [\n{"row_words": 64, "batch_class": %d, "n_class": %d, "kernel": 5, '
+                    '"tensor_mode": 2, "tensor_kc_rows": 32768, "tensor_loads": %d}\n]}\n'
+                    % (bclass, nclass, loads))
+    talekpir.tune_load(str(plan))
+    try:
+        exp = oracle.read(T, n, d, z, R[0])
+        assert exp[0:4].any() == (((n - 1) % 2) == 1)
+        with _db(n, d, z, T) as db:
+            got = db.read_batch(R)
+        assert (got == exp[None, :]).all()
+    finally:
+        talekpir.tune_clear()
+    assert talekpir.device_status() == talekpir.OK
+
+
 @pytest.mark.parametrize("n,B", [(32768, 256), (40003, 129), (70001, 300), (65, 7),
                                  (131075, 64)])
 def test_tensor_kernel_exact_counts_all_ones(n, B):
