@@ -23,6 +23,7 @@ weak scaling.  `--impl reference` times the CPU oracle instead.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -52,7 +53,8 @@ TRAFFIC_BATCHED_B256 = (136.659968e6 + 3.284480e6 + 136.435200e6 + 0.130304e6 + 
 TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
 TRAFFIC_M4RM_B256 = (136.340736e6 + 3.074048e6 + 136.585216e6 + 0.072192e6 + 136.370944e6
                      + 0.116480e6) / 3
-TRAFFIC_GF2MMA_B256 = None  # no ncu capture of the current tensor-core kernel yet
+TRAFFIC_GF2MMA_B256 = (135.390208e6 + 3.474432e6 + 135.348992e6 + 0.136960e6 + 135.354880e6
+                       + 0.129024e6) / 3
 
 
 def measured_peaks() -> dict:
@@ -603,7 +605,11 @@ def writes_leg(talekpir, synth) -> dict:
     the slots (the load of the paper's cost table), at most 500 evictions: the
     table is first filled to 90 %, then 4096 writes are timed in batches of
     256 (tpir_write_batch: host placement, then the slot moves and payloads on
-    the device) and 256 more one by one (tpir_write); interest vectors of
+    the device) and 256 more one by one (tpir_write: host time per call, the
+    moves and message travelling in the launch), then 256 each followed by a
+    wait for its completion (tpir_db_sync) and 256 through tpir_write_noalloc
+    (message in a device buffer) each followed by a wait on its stream: the
+    medians are the completion latencies; interest vectors of
     m = 2^20 bits, k = 4, 65 536 writes' positions per call.  The calls are
     synchronous: host wall-clock."""
     n, d, z = N_BUCKETS, D_SLOTS, MSG_BYTES
@@ -612,7 +618,7 @@ def writes_leg(talekpir, synth) -> dict:
     timed_batch, timed_single, per = 4096, 256, 256
     db = talekpir.DB(n, d, z)
     db.set_policy(cap, 500, 11)
-    keys = synth.write_keys(fill + timed_batch + timed_single, seed=12)
+    keys = synth.write_keys(fill + timed_batch + 3 * timed_single, seed=12)
     b1, b2 = synth.bucket_pairs(keys, n)
     M = synth.messages(4096, z, seed=12)  # payload bytes do not change the cost
     for i in range(0, fill, 4096):
@@ -630,7 +636,34 @@ def writes_leg(talekpir, synth) -> dict:
         rc, ev = db.write(int(b1[i]), int(b2[i]), M[i % 4096])
         ev_total += ev
         efull += int(rc != talekpir.OK)
+    db.sync()
     ts = time.perf_counter() - t0
+    # completion latency: each write followed by a wait for its moves
+    lat = []
+    base = fill + timed_batch + timed_single
+    for i in range(base, base + timed_single):
+        t1 = time.perf_counter()
+        rc, ev = db.write(int(b1[i]), int(b2[i]), M[i % 4096])
+        db.sync()
+        lat.append(time.perf_counter() - t1)
+        ev_total += ev
+        efull += int(rc != talekpir.OK)
+    # the write that allocates nothing: message from a device buffer, moves
+    # in the launch, on a caller's stream; completion latency per call
+    import torch
+    nstream = torch.cuda.Stream()
+    dM = torch.from_numpy(M[:timed_single]).cuda()
+    lat_na = []
+    base += timed_single
+    for j, i in enumerate(range(base, base + timed_single)):
+        t1 = time.perf_counter()
+        ev_na = ctypes.c_uint32(0)
+        rc = talekpir.lib().tpir_write_noalloc(db.h, int(b1[i]), int(b2[i]), dM[j].data_ptr(),
+                                               ctypes.byref(ev_na), nstream.cuda_stream)
+        nstream.synchronize()
+        lat_na.append(time.perf_counter() - t1)
+        ev_total += ev_na.value
+        efull += int(rc != talekpir.OK)
     db.bloom_create(1 << 20, 4, 1, 0)
     pos = synth.bloom_positions(keys[:65536], 1 << 20, 4)
     assert db.bloom_insert_batch(pos) == talekpir.OK
@@ -643,7 +676,9 @@ def writes_leg(talekpir, synth) -> dict:
             "batched_writes_per_s": timed_batch / tb, "batch": per,
             "batched_us_per_write": tb / timed_batch * 1e6,
             "single_write_us": ts / timed_single * 1e6,
-            "mean_evictions": ev_total / (timed_batch + timed_single), "efull": efull,
+            "single_write_latency_us": statistics.median(lat) * 1e6,
+            "noalloc_write_latency_us": statistics.median(lat_na) * 1e6,
+            "mean_evictions": ev_total / (timed_batch + 3 * timed_single), "efull": efull,
             "interest_vector_updates_per_s": 65536 / tbl, "interest_vector_m_bits": 1 << 20,
             "interest_vector_k": 4}
 
@@ -725,21 +760,32 @@ def multi_leg(talekpir, synth, torch, stream, args) -> dict:
         total_bytes += n * d * z
         reads += B
         ops += B * n * d * z // 4
+    def graph_time():
+        g = talekpir.MultiGraph(jobs)
+        for _ in range(args.warmup):
+            g.launch(stream)
+        ms = _events_ms(torch, stream, lambda: g.launch(stream), max(3, args.steps))
+        g.close()
+        return ms
+
+    # the built-in choices first, then the autotuner's: one trial per (row
+    # width, batch-size class), on the class's smallest table (larger tables
+    # take the plan of the nearest size class)
+    graph_ms_builtin = graph_time()
     tuned = 0
+    kernels_chosen = {}
     if not args.no_autotune:
-        # one trial per (row width, batch-size class), on the class's smallest table
         seen = {}
         for (db, B, R, O) in jobs:
             key = (db.row_bytes, max(1, (B - 1).bit_length()))
             if key not in seen or db.n < seen[key][0].n:
                 seen[key] = (db, B)
         for db, B in seen.values():
-            db.autotune(B, reps=2)
+            r = db.autotune(B, reps=2)
+            k = {1: "plain", 2: "lop3", 4: "four_russians", 5: "tensor"}.get(r["kernel"], str(r["kernel"]))
+            kernels_chosen[k] = kernels_chosen.get(k, 0) + 1
         tuned = len(seen)
-    g = talekpir.MultiGraph(jobs)
-    for _ in range(args.warmup):
-        g.launch(stream)
-    graph_ms = _events_ms(torch, stream, lambda: g.launch(stream), max(3, args.steps))
+    graph_ms = graph_time() if tuned else graph_ms_builtin
 
     def separate():
         for (db, B, R, O) in jobs:
@@ -747,12 +793,14 @@ def multi_leg(talekpir, synth, torch, stream, args) -> dict:
     for _ in range(2):
         separate()
     sep_ms = _events_ms(torch, stream, separate, max(2, args.steps // 2))
-    g.close()
+    talekpir.tune_clear()
     for db in dbs:
         db.close()
     return {"tables": len(shapes), "table_bytes": total_bytes, "reads": reads,
-            "tuned_classes": tuned,
+            "tuned_classes": tuned, "tuned_kernels": kernels_chosen,
+            "graph_ms_builtin_choice": graph_ms_builtin,
             "graph_ms": graph_ms, "separate_ms": sep_ms,
+            "tuning_gain": graph_ms_builtin / graph_ms - 1.0,
             "reads_per_s_graph": reads / (graph_ms * 1e-3),
             "reads_per_s_separate": reads / (sep_ms * 1e-3),
             # 32-bit XOR-AND operations of the plain product per second (the

@@ -95,6 +95,10 @@ tpir_status tpir_shard_plan(uint64_t n_total, uint32_t parts, uint32_t index, ui
 tpir_status tpir_db_info(const tpir_db *db, uint64_t *n, uint32_t *d, uint32_t *msg_bytes,
                          const void **d_table, uint64_t *epoch);
 
+/* Blocks until every write, load and read already submitted on this db (on
+ * its own stream or any other) has completed on the device. */
+tpir_status tpir_db_sync(tpir_db *db);
+
 /* Cuckoo policy (Section 5.3): keep at most `capacity` messages, collecting
  * the oldest first (0 = never collect); give up an eviction walk after
  * `max_evictions` evictions; s_cuckoo seeds the random choices (splitmix64),
@@ -242,10 +246,10 @@ tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
  * and keeps (a) the fastest tile shape for every later launch of the
  * register-tiled kernel with this row width and batch-size class
  * (ceil(log2 B)), and (b) the fastest kernel, with its tensor-core schedule,
- * for every later automatic choice with this row width, batch class and
- * table-size class (ceil(log2 n)): single-table reads, many-table launches
- * and the serve loop then take the measured winner instead of the built-in
- * batch thresholds.  reps = timed launches per candidate (0 = 3).  Allocates
+ * for every later automatic choice with this row width and batch class
+ * (tables of another size take the plan of the nearest table-size class,
+ * ceil(log2 n)): single-table reads, many-table launches and the serve loop
+ * then take the measured winner instead of the built-in batch thresholds.  reps = timed launches per candidate (0 = 3).  Allocates
  * scratch buffers for the trial requests and replies. */
 typedef struct {
     uint32_t lw_log2, warps_b, warps_w, warps_k, stage_rows;

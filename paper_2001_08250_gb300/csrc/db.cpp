@@ -587,6 +587,15 @@ tpir_status tpir_db_info(const tpir_db* db, uint64_t* n, uint32_t* d, uint32_t* 
   return TPIR_OK;
 }
 
+tpir_status tpir_db_sync(tpir_db* db) {
+  if (!db) return TPIR_EINVAL;
+  cudaError_t e = cudaEventSynchronize(db->last_write);
+  for (auto& pr : db->read_events)
+    if (e == cudaSuccess) e = cudaEventSynchronize(pr.second);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(db->stream);
+  return cuda_status(e);
+}
+
 tpir_status tpir_db_set_policy(tpir_db* db, uint64_t capacity, uint32_t max_evictions,
                                uint64_t s_cuckoo) {
   if (!db) return TPIR_EINVAL;

@@ -983,7 +983,40 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
   const uint64_t per_cta = (units + grid - 1) / grid;
   const uint32_t mode = sched ? sched->mode : 0u;
   const bool span_ok = per_cta <= kGMaxCount / kGKStage;
-  if (span_ok && mode != 2) {
+  // Item mode: items of whole k-chunks, taken round by round so that the
+  // CTAs of a round read the same rows (each row leaves DRAM once, the
+  // request words are shared in L2); k-chunks minimise rounds x item time on
+  // the grid, item time ~ MMAs (about 122 cycles each) + epilogue, which the
+  // second accumulator hides when an item holds one M-tile.
+  const double mts = B <= 128 ? 1.0 : 2.0;
+  const double epi = L.nbuf == 2 ? 600.0 : 3000.0;
+  const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
+  const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
+  double best = 1e300;
+  uint64_t best_rows = kGKStage, best_rounds = 1;
+  for (uint64_t c = std::max<uint64_t>(1, min_kc);
+       c <= std::max<uint64_t>(min_kc, std::min<uint64_t>(max_kc, 512)); ++c) {
+    const uint64_t rows = g_clamp_rows((n + c - 1) / c, n);
+    const uint64_t kcs = (n + rows - 1) / rows;
+    const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
+    const uint64_t rounds = (items + grid - 1) / grid;
+    const double cost =
+        static_cast<double>(rounds) * (static_cast<double>(rows) / kGKStep * mts * 122.0 + epi);
+    if (cost < best) {
+      best = cost;
+      best_rows = rows;
+      best_rounds = rounds;
+    }
+  }
+  // Planned choice: items when their rounds keep every CTA about as busy as
+  // equal spans would (within 10 %), else spans (when admissible).
+  bool use_span = span_ok;
+  if (mode == 1) use_span = span_ok;
+  else if (mode == 2) use_span = false;
+  else if (span_ok)
+    use_span = static_cast<double>(best_rounds * ((best_rows + kGKStage - 1) / kGKStage)) >
+               1.1 * static_cast<double>(per_cta);
+  if (use_span) {
     // span mode: equal runs of stages per CTA, strip-major; partial strips of
     // several CTAs XOR-reduce into replies initialised first
     L.span = 1;
@@ -992,30 +1025,6 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
     J.split = 1;
     L.total_items = 0;
   } else {
-    // item mode (long spans): items of whole k-chunks, taken round by round
-    // so that the CTAs of a round read the same rows; k-chunks minimise
-    // rounds x item time on the grid, item time ~ MMAs (about 122 cycles
-    // each) + epilogue, which the second accumulator hides when an item
-    // holds one M-tile
-    const double mts = B <= 128 ? 1.0 : 2.0;
-    const double epi = L.nbuf == 2 ? 600.0 : 3000.0;
-    const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
-    const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
-    double best = 1e300;
-    uint64_t best_rows = kGKStage;
-    for (uint64_t c = std::max<uint64_t>(1, min_kc);
-         c <= std::max<uint64_t>(min_kc, std::min<uint64_t>(max_kc, 512)); ++c) {
-      const uint64_t rows = g_clamp_rows((n + c - 1) / c, n);
-      const uint64_t kcs = (n + rows - 1) / rows;
-      const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
-      const uint64_t rounds = (items + grid - 1) / grid;
-      const double cost = static_cast<double>(rounds) *
-                          (static_cast<double>(rows) / kGKStep * mts * 122.0 + epi);
-      if (cost < best) {
-        best = cost;
-        best_rows = rows;
-      }
-    }
     J.kc_rows = static_cast<uint32_t>(best_rows);
     if (mode == 2 && sched->kc_rows) J.kc_rows = g_clamp_rows(sched->kc_rows, n);
     const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;

@@ -13,6 +13,7 @@
 // instead of the built-in batch thresholds.  Both caches can be saved to and
 // loaded from a small JSON file.
 #include <cstdio>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -78,12 +79,27 @@ bool plan_lookup(uint32_t Wd, uint32_t B, Shape* out) {
   return true;
 }
 
+// The plan of the same row width and batch class whose table-size class is
+// nearest (exact first; a tie takes the smaller tables' plan).
 bool kernel_plan_lookup(uint32_t Wd, uint32_t B, uint64_t n, KernelPlan* out) {
   std::lock_guard<std::mutex> g(g_plan_mu);
   if (g_kplans.empty()) return false;
-  auto it = g_kplans.find(std::make_tuple(Wd, bclass(B), nclass(n)));
-  if (it == g_kplans.end()) return false;
-  *out = it->second;
+  const uint32_t bc = bclass(B), nc = nclass(n);
+  auto hi = g_kplans.lower_bound(std::make_tuple(Wd, bc, nc));
+  auto best = g_kplans.end();
+  uint32_t dist = ~0u;
+  if (hi != g_kplans.end() && std::get<0>(hi->first) == Wd && std::get<1>(hi->first) == bc) {
+    best = hi;
+    dist = std::get<2>(hi->first) - nc;
+  }
+  if (hi != g_kplans.begin()) {
+    auto lo = std::prev(hi);
+    if (std::get<0>(lo->first) == Wd && std::get<1>(lo->first) == bc &&
+        nc - std::get<2>(lo->first) <= dist)
+      best = lo;
+  }
+  if (best == g_kplans.end()) return false;
+  *out = best->second;
   return true;
 }
 

@@ -83,6 +83,7 @@ _SIGS = [
     ("tpir_shard_plan", ctypes.c_int, [_u64, _u32, _u32, _vp, _vp]),
     ("tpir_db_info", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("tpir_db_set_policy", ctypes.c_int, [_vp, _u64, _u32, _u64]),
+    ("tpir_db_sync", ctypes.c_int, [_vp]),
     ("tpir_db_load", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("tpir_db_load_async", ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp]),
     ("tpir_db_dump", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
@@ -238,6 +239,10 @@ class DB:
 
     def set_policy(self, capacity: int = 0, max_evictions: int = 500, seed: int = 0) -> None:
         _check(lib().tpir_db_set_policy(self.h, capacity, max_evictions, seed), "tpir_db_set_policy")
+
+    def sync(self) -> None:
+        """Wait until every write and read submitted on this table has completed."""
+        _check(lib().tpir_db_sync(self.h), "tpir_db_sync")
 
     def set_kernel(self, kernel: int) -> None:
         _check(lib().tpir_db_set_kernel(self.h, kernel), "tpir_db_set_kernel")
