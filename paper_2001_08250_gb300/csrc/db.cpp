@@ -172,7 +172,8 @@ tpir_status enqueue_read(tpir_db* db, const uint64_t* d_req, uint32_t B, void* d
     }
   } else if (kernel == 5) {
     KernelPlan kp;
-    const bool planned = kernel_plan_lookup(db->Wd, B, db->n, &kp) && kp.kernel == 5;
+    bool exact = false;
+    const bool planned = kernel_plan_lookup(db->Wd, B, db->n, &kp, &exact) && kp.kernel == 5 && exact;
     e = tcopy_ensure(db, st);
     if (e == cudaSuccess)
       e = launch_gf2_mma(db->d_tt, db->n, db->Wd, d_req, db->words64, B,
@@ -234,9 +235,18 @@ tpir_status apply_writes_core(tpir_db* db, uint32_t count, const uint64_t* b1, c
   if (!ops.empty()) {
     const uint64_t pay_bytes = count * z;
     cudaError_t e = cudaSuccess;
-    if (ops.size() <= kParamOps && pay_bytes <= kParamBytes) {
-      // small batch (a single write): moves and messages by value in the
-      // kernel parameters, one launch, no staging to wait for
+    if (ops.size() <= ParamMovesS::kOps && pay_bytes <= ParamMovesS::kBytes) {
+      // a single write of a slot up to 4 KiB: moves and message by value in a
+      // small parameter block, one launch, no staging to wait for
+      thread_local ParamMovesS m;
+      m.nops = static_cast<uint32_t>(ops.size());
+      m.pad = 0;
+      std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
+      std::memcpy(m.payload, msgs, pay_bytes);
+      e = launch_apply_moves_param(db->d_table, db->z, m, db->d_tmp, st);
+      if (e == cudaSuccess) e = tcopy_after_moves(db, ops.data(), ops.size(), st);
+    } else if (ops.size() <= kParamOps && pay_bytes <= kParamBytes) {
+      // small batch: the same with the larger parameter block
       thread_local ParamMoves m;
       m.nops = static_cast<uint32_t>(ops.size());
       m.pad = 0;
@@ -358,7 +368,8 @@ tpir_status enqueue_multi(const tpir_read_job* jobs, uint32_t njobs, cudaStream_
       M4Request t = r;
       t.Tt = q.db->d_tt;
       KernelPlan kp;
-      if (kernel_plan_lookup(q.db->Wd, q.B, q.db->n, &kp) && kp.kernel == 5) {
+      bool exact = false;
+      if (kernel_plan_lookup(q.db->Wd, q.B, q.db->n, &kp, &exact) && kp.kernel == 5 && exact) {
         if (kp.sched.mode == 2) t.kc_rows = kp.sched.kc_rows;
         t.loads = kp.sched.loads;
       }

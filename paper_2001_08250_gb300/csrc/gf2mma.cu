@@ -125,7 +125,9 @@ struct GJob {
   uint32_t n_strips, n_mb, kc_rows;
   uint32_t stages;       // stages (kGKStage buckets) per strip: ceil(n / kGKStage)
   uint32_t item_begin;   // index of this job's first item in the launch
-  uint32_t split;        // replies are initialised first and XOR-reduced into
+  uint32_t split;        // 0: replies stored; 1: initialised first (zeros or masks)
+                         // and XOR-reduced into; 2: masked, stored by their single
+                         // writer (one k-chunk, items) with the mask XORed in
   uint32_t req_tma;      // request words staged by TMA: 0 no, 1 rows, 2 row pairs
   uint32_t req_box;      // rows of the request box (RM 1: min(B, 256); RM 2: even rows)
   uint32_t req_box_o;    // RM 2: rows of the odd-row box (0: B = 1, no odd rows)
@@ -365,6 +367,15 @@ __device__ __forceinline__ void g_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Word i (0..15) of a keystream block, by selects (the index is not known at
+// compile time; a register array indexed at run time would go to local memory)
+__device__ __forceinline__ uint32_t g_pick(const uint32_t (&k)[16], uint32_t i) {
+  uint32_t v = k[0];
+#pragma unroll
+  for (uint32_t j = 1; j < 16; ++j) v = i == j ? k[j] : v;
+  return v;
+}
+
 // Parity words of `nw` (<= 7) consecutive reply words (w0 ..) for request b
 // from the accumulator columns at taddr (column 32 c + j = bit j of word
 // w0 + c): each value is an exact count; adding 2^23 puts it in the
@@ -388,10 +399,28 @@ __device__ __forceinline__ void g_epilogue(const GJob& J, uint32_t taddr, uint32
   }
   if (b >= J.B) return;
   uint32_t* o = J.out + static_cast<uint64_t>(b) * J.Wd + w0;
+  if (J.split == 2) {
+    // a masked reply word with this thread its only writer: XOR in the
+    // request's keystream (ChaCha20 block w / 16, word w % 16; the seven words
+    // span at most two blocks)
+    const uint4* k4 = reinterpret_cast<const uint4*>(J.seeds + static_cast<uint64_t>(b) * 32);
+    const uint4 ka = __ldg(k4), kb = __ldg(k4 + 1);
+    const uint32_t key[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+    const uint32_t blk0 = w0 >> 4;
+    uint32_t k0[16], k1[16];
+    cc_block(key, blk0, k0);
+    cc_block(key, blk0 + 1, k1);
+#pragma unroll
+    for (uint32_t c = 0; c < kGStripWords; ++c) {
+      const uint32_t w = w0 + c;
+      const uint32_t m = (w >> 4) == blk0 ? g_pick(k0, w & 15u) : g_pick(k1, w & 15u);
+      pw[c] ^= m;
+    }
+  }
 #pragma unroll
   for (uint32_t c = 0; c < kGStripWords; ++c) {
     if (c < nw && w0 + c < J.Wd) {
-      if (J.split)
+      if (J.split == 1)
         g_red_xor32(o + c, pw[c]);
       else
         o[c] = pw[c];
@@ -446,12 +475,16 @@ __device__ __forceinline__ bool g_req_step(const GLaunch<NJ>& L, const GCursor& 
     const uint32_t base = raw0 + rs * kGRawBytes + kGRawTable;
     uint64_t y[kGStageWords];
     if constexpr (RM == 1) {
-      const uint32_t a = base + q * 32u;
-      const uint4 v0 = ld_shared_v4(a), v1 = ld_shared_v4(a + 16u);
-      y[0] = v0.x | static_cast<uint64_t>(v0.y) << 32;
-      y[1] = v0.z | static_cast<uint64_t>(v0.w) << 32;
-      y[2] = v1.x | static_cast<uint64_t>(v1.y) << 32;
-      y[3] = v1.z | static_cast<uint64_t>(v1.w) << 32;
+      // rows are 32 bytes apart: lanes 4..7 of each group of eight read their
+      // second 16 bytes first, so a quarter-warp's loads hit eight distinct
+      // 16-byte bank groups
+      const uint32_t a = base + q * 32u, h = (q >> 2) & 1u;
+      const uint4 v0 = ld_shared_v4(a + 16u * h), v1 = ld_shared_v4(a + 16u * (h ^ 1u));
+      const uint4 lo = h ? v1 : v0, hi = h ? v0 : v1;
+      y[0] = lo.x | static_cast<uint64_t>(lo.y) << 32;
+      y[1] = lo.z | static_cast<uint64_t>(lo.w) << 32;
+      y[2] = hi.x | static_cast<uint64_t>(hi.y) << 32;
+      y[3] = hi.z | static_cast<uint64_t>(hi.w) << 32;
     } else {
       // request q of the block: even rows' words at their pair's 32 bytes,
       // odd rows' at bytes 8 .. 39 of their pair's 48
@@ -867,7 +900,7 @@ __global__ void gf2_init_kernel(const __grid_constant__ GLaunch<NJ> L) {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const GJob& J = L.jobs[blockIdx.y];
-  if (!J.split) return;
+  if (J.split != 1) return;
   init_replies(reinterpret_cast<uint4*>(J.out), J.B, J.Wd / 4, J.seeds,
                blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
@@ -950,8 +983,8 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
   }
   int* status = device_status_word();
   if (!status) return cudaErrorInvalidSymbol;
-  bool any = false;
-  for (uint32_t i = 0; i < L.njobs; ++i) any |= L.jobs[i].split != 0;
+  bool any = false;  // replies to initialise before the scan XOR-reduces into them
+  for (uint32_t i = 0; i < L.njobs; ++i) any |= L.jobs[i].split == 1;
   cudaError_t e = cudaSuccess;
   if (any) e = launch_pdl(gf2_init_kernel<NJ>, dim3(64, L.njobs), dim3(256), 0, st, L);
   if (e != cudaSuccess) return e;
@@ -1030,7 +1063,7 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
     const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;
     const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
     if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
-    J.split = (kcs > 1 || seeds) ? 1u : 0u;
+    J.split = kcs > 1 ? 1u : seeds ? 2u : 0u;
     L.total_items = static_cast<uint32_t>(items);
   }
   J.item_begin = 0;
@@ -1075,7 +1108,7 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode,
     j.kc_rows = src[i]->kc_rows ? g_clamp_rows(src[i]->kc_rows, j.n)
                                 : g_clamp_rows(static_cast<uint64_t>(target / mt), j.n);
     const uint64_t kcs = (j.n + j.kc_rows - 1) / j.kc_rows;
-    j.split = (kcs > 1 || j.seeds) ? 1u : 0u;
+    j.split = kcs > 1 ? 1u : j.seeds ? 2u : 0u;
     cost[i] = static_cast<double>(std::min<uint64_t>(j.kc_rows, j.n)) * mt;
   }
   std::vector<size_t> order(js.size());

@@ -81,7 +81,7 @@ bool plan_lookup(uint32_t Wd, uint32_t B, Shape* out) {
 
 // The plan of the same row width and batch class whose table-size class is
 // nearest (exact first; a tie takes the smaller tables' plan).
-bool kernel_plan_lookup(uint32_t Wd, uint32_t B, uint64_t n, KernelPlan* out) {
+bool kernel_plan_lookup(uint32_t Wd, uint32_t B, uint64_t n, KernelPlan* out, bool* exact) {
   std::lock_guard<std::mutex> g(g_plan_mu);
   if (g_kplans.empty()) return false;
   const uint32_t bc = bclass(B), nc = nclass(n);
@@ -100,6 +100,7 @@ bool kernel_plan_lookup(uint32_t Wd, uint32_t B, uint64_t n, KernelPlan* out) {
   }
   if (best == g_kplans.end()) return false;
   *out = best->second;
+  if (exact) *exact = std::get<2>(best->first) == nc;
   return true;
 }
 

@@ -37,9 +37,10 @@ __global__ void __launch_bounds__(256) apply_moves_kernel(uint8_t* __restrict__ 
 // The same moves for a small batch of writes, with the move list and the new
 // messages passed by value in the kernel parameters: no staging buffer, no
 // copy before the launch, so a single write costs one launch.
+template <typename PM>
 __global__ void __launch_bounds__(256) apply_moves_param_kernel(uint8_t* __restrict__ table,
                                                                 uint32_t z,
-                                                                const __grid_constant__ ParamMoves m,
+                                                                const __grid_constant__ PM m,
                                                                 uint8_t* __restrict__ tmp) {
   const uint32_t z4 = z / 16;
   for (uint32_t i = 0; i < m.nops; ++i) {
@@ -100,7 +101,14 @@ cudaError_t launch_apply_moves(uint8_t* table, uint32_t z, const MoveOp* ops, ui
 cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMoves& m, uint8_t* tmp,
                                      cudaStream_t st) {
   if (m.nops == 0) return cudaSuccess;
-  apply_moves_param_kernel<<<1, 256, 0, st>>>(table, z, m, tmp);
+  apply_moves_param_kernel<ParamMoves><<<1, 256, 0, st>>>(table, z, m, tmp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMovesS& m, uint8_t* tmp,
+                                     cudaStream_t st) {
+  if (m.nops == 0) return cudaSuccess;
+  apply_moves_param_kernel<ParamMovesS><<<1, 256, 0, st>>>(table, z, m, tmp);
   return cudaGetLastError();
 }
 

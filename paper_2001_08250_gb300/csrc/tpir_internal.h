@@ -105,7 +105,10 @@ struct KernelPlan {
   int kernel = 0;
   GSched sched;
 };
-bool kernel_plan_lookup(uint32_t Wd, uint32_t B, uint64_t n, KernelPlan* out);
+// *exact (if given): the plan was tuned for this table-size class; plans of
+// another size class lend their kernel choice, not their schedule.
+bool kernel_plan_lookup(uint32_t Wd, uint32_t B, uint64_t n, KernelPlan* out,
+                        bool* exact = nullptr);
 int scan_stage_bytes(const Shape& s);
 
 // Launch with programmatic dependent launch (PDL) allowed: the kernel may
@@ -165,18 +168,25 @@ constexpr uint64_t kTmpSlot = ~0ull;
 cudaError_t launch_apply_moves(uint8_t* table, uint32_t z, const MoveOp* ops, uint32_t nops,
                                const uint8_t* payloads, uint8_t* tmp, cudaStream_t st);
 // A small batch of writes with its moves and new messages in the kernel
-// parameters (no staging): at most kParamOps moves and kParamBytes of
-// messages (payload index i = bytes i*z .. of `payload`).
-constexpr uint32_t kParamOps = 384;
-constexpr uint32_t kParamBytes = 20 * 1024;
-struct ParamMoves {
+// parameters (no staging): at most OPS moves and BYTES of messages (payload
+// index i = bytes i*z .. of `payload`).  Two sizes: the launch copies the whole
+// parameter block, so a single write of a slot up to 4 KiB takes the small one.
+template <uint32_t OPS, uint32_t BYTES>
+struct ParamMovesT {
+  static constexpr uint32_t kOps = OPS, kBytes = BYTES;
   uint32_t nops;
   uint32_t pad;
-  MoveOp ops[kParamOps];
-  __align__(16) uint8_t payload[kParamBytes];
+  MoveOp ops[OPS];
+  __align__(16) uint8_t payload[BYTES];
 };
+using ParamMovesS = ParamMovesT<48, 4096>;
+using ParamMoves = ParamMovesT<384, 20 * 1024>;
+constexpr uint32_t kParamOps = ParamMoves::kOps;
+constexpr uint32_t kParamBytes = ParamMoves::kBytes;
 static_assert(sizeof(ParamMoves) + 64 < 32000, "kernel parameters must stay below 32 KB");
 cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMoves& m, uint8_t* tmp,
+                                     cudaStream_t st);
+cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMovesS& m, uint8_t* tmp,
                                      cudaStream_t st);
 cudaError_t launch_bloom_set(uint64_t* delta, const uint64_t* pos, uint64_t count, cudaStream_t st);
 cudaError_t launch_bloom_or(uint64_t* delta, const uint64_t* vec, uint64_t m, cudaStream_t st);
