@@ -53,8 +53,8 @@ TRAFFIC_BATCHED_B256 = (136.659968e6 + 3.284480e6 + 136.435200e6 + 0.130304e6 + 
 TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
 TRAFFIC_M4RM_B256 = (136.340736e6 + 3.074048e6 + 136.585216e6 + 0.072192e6 + 136.370944e6
                      + 0.116480e6) / 3
-TRAFFIC_GF2MMA_B256 = (135.390208e6 + 3.474432e6 + 135.348992e6 + 0.136960e6 + 135.354880e6
-                       + 0.129024e6) / 3
+TRAFFIC_GF2MMA_B256 = (135.352320e6 + 2.965248e6 + 135.358208e6 + 0.170496e6 + 135.383296e6
+                       + 0.146176e6) / 3
 
 
 def measured_peaks() -> dict:

@@ -23,23 +23,26 @@
 // columns (two M-tiles of one item, or one M-tile of two items
 // double-buffered) and the scale factors in columns 448..511.
 //
-// Data flow per CTA (persistent, one per SM, 800 threads):
-//   warp 15     streams, by 2-D TMA, each stage's 4 words of the strip's 224
+// Data flow per CTA (persistent, one per SM, 896 threads):
+//   warp 0      streams, by 2-D TMA, each stage's 4 words of the strip's 224
 //               columns of the transposed table and the stage's 4 words of
 //               the item's requests into a ring of raw stages: rows of an
 //               even number of 64-bit words as rows, of an odd number as row
 //               pairs (TMA boxes start 16-byte aligned); per-thread loads for
 //               a request buffer that is not 16-byte aligned;
-//   warps 0-6   table expanders: lane = column; its 256 bits of the stage
-//               become 128 bytes of e2m1 (the column's row of the B operand);
-//   warps 7-14  request expanders: lane = request q of the item's (up to)
-//               256; its 256 bits of the stage become its A operand row;
+//   7 warps     table expanders (warps 1, 5, 9, 13, 3, 7, 11): lane = column;
+//               its 256 bits of the stage become 128 bytes of e2m1 (the
+//               column's row of the B operand);
+//   8 warps     request expanders (warps 25, 2, 6, 10, 14, 26, 15, 27): lane =
+//               request q of the item's (up to) 256; its 256 bits of the
+//               stage become its A operand row;
 //   warp 24     one thread issues the MMAs of each stage and commits them to
-//               the stage's "empty" barrier;
+//               the stage's "empty" barrier as soon as they are issued;
 //   warps 16-23 epilogue: read the accumulators (tcgen05.ld), take each sum's
 //               parity, and store (single k-chunk) or XOR-reduce (split, or a
 //               masked read) the reply words; two groups of four warps split
-//               an item (one M-tile, or four / three of its seven words).
+//               an item (one M-tile, or four / three of its seven words);
+//   warps 4, 8, 12 idle.
 // Both operands use one order of the buckets within a 32-bucket chunk:
 // element 8 t + m of the chunk (nibble m of its 32-bit word t) is bucket
 // 4 m + t, so a word's 32 bits become their 32 nibbles with one shift and
@@ -78,9 +81,32 @@ constexpr int kGStageBytes = 2 * kGTileA + kGTileB;
 // (k / 16) kGLbo + (r % 8) 16.
 constexpr int kGLbo = 128;
 constexpr int kGSbo = (kGRowBytes / 16) * 128;
-constexpr uint32_t kGTableWarps = 7, kGReqWarp0 = 7, kGReqWarps = 8;
-constexpr uint32_t kGTmaWarp = 15, kGEpiWarp0 = 16, kGIssueWarp = 24;
-constexpr int kGThreads = 25 * 32;
+constexpr uint32_t kGTableWarps = 7, kGReqWarps = 8;
+constexpr uint32_t kGTmaWarp = 0, kGEpiWarp0 = 16, kGIssueWarp = 24;
+constexpr int kGThreads = 28 * 32;
+// Roles by SM sub-partition (warp w issues from sub-partition w % 4).  The
+// MMA thread (warp 24) issues from sub-partition 0, and any expander placed
+// there fell up to a pipeline stage behind the rest (its shared-memory
+// traffic queued behind the tensor-core instructions) while every stage waits
+// for its last expander.  So sub-partition 0 holds only the TMA producer (0),
+// the epilogue warps 16 and 20 and the MMA thread; the 15 expanders share
+// sub-partitions 1-3 (five each): table columns 32 i + lane on warps 1, 5, 9,
+// 13, 3, 7, 11 (i = 0..6), requests 32 i + lane on warps 25, 2, 6, 10, 14,
+// 26, 15, 27 (i = 0..7).
+__device__ __forceinline__ int g_table_index(uint32_t warp) {
+  switch (warp) {
+    case 1: return 0; case 5: return 1; case 9: return 2; case 13: return 3;
+    case 3: return 4; case 7: return 5; case 11: return 6;
+    default: return -1;
+  }
+}
+__device__ __forceinline__ int g_req_index(uint32_t warp) {
+  switch (warp) {
+    case 25: return 0; case 2: return 1; case 6: return 2; case 10: return 3;
+    case 14: return 4; case 26: return 5; case 15: return 6; case 27: return 7;
+    default: return -1;
+  }
+}
 constexpr int kGRawTable = kGCols * kGStageWords * 8;  // 4 words of 224 columns: 7 KiB
 // Raw stages (table words + request words) by request-staging mode RM:
 // RM = 1: 256 request rows x 32 bytes; RM = 2 (rows of an odd number of
@@ -620,11 +646,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
       }
     }
-  } else if (warp < kGTableWarps) {
+  } else if (g_table_index(warp) >= 0) {
     // ------------------------ table expanders ------------------------
     // lane = column 32 warp + lane of the strip: its 4 words of the stage
     // (buckets ks .. ks + 255) become its 128-byte row of the B operand
-    const uint32_t col = 32u * warp + lane;
+    const uint32_t col = 32u * static_cast<uint32_t>(g_table_index(warp)) + lane;
     uint32_t iter = 0;
     for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter) {
       const uint32_t rs = iter % kGRaw, rph = (iter / kGRaw) & 1u;
@@ -656,22 +682,22 @@ __global__ void __launch_bounds__(kGThreads, 1)
       __syncwarp();
       if (lane == 0) mb::arrive(&full[s]);
     }
-  } else if (warp < kGReqWarp0 + kGReqWarps && RM != 0) {
+  } else if (g_req_index(warp) >= 0 && RM != 0) {
     // ------------------- request expanders (TMA-staged words) -------------------
     // Thread q takes request q of the item's (up to) 256.
-    const uint32_t q = threadIdx.x - 32u * kGReqWarp0;
+    const uint32_t q = 32u * static_cast<uint32_t>(g_req_index(warp)) + lane;
     uint32_t iter = 0;
     const uint64_t none[kGStageWords] = {0, 0, 0, 0};
     for (GCursor c = g_cur_start(L); c.valid; g_cur_next(c, L), ++iter)
       if (!g_req_step<NJ, RM>(L, c, none, iter, q, lane, stage0, raw0, full, empty, raw_full, raw_empty,
                              abort_flag, status))
         break;
-  } else if (warp < kGReqWarp0 + kGReqWarps) {
+  } else if (g_req_index(warp) >= 0) {
     // ------------------------ request expanders ------------------------
     // Thread q takes request q of the item's (up to) 256, loaded from global
     // memory into three register sets, each loaded three stages ahead of its
     // use so that a stage does not wait on their (L2) latency.
-    const uint32_t q = threadIdx.x - 32u * kGReqWarp0;
+    const uint32_t q = 32u * static_cast<uint32_t>(g_req_index(warp)) + lane;
     GCursor ca = g_cur_start(L);
     GCursor cb = ca;
     g_cur_next(cb, L);
@@ -756,17 +782,17 @@ __global__ void __launch_bounds__(kGThreads, 1)
                     j ? 1u : acc0);
             }
           }
-          bool next_ok = true;
-          if (more) {
-            next_ok = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          }
           {
             const uint32_t q = total - 1, j = q / it.mt, t = q % it.mt;
             g_mma(acc + kGCols * t, sa + kDescTile * t + kDescK * j, sb + kDescK * j, sfa, sfb,
                   j ? 1u : acc0);
           }
           g_commit(&empty[s]);
+          bool next_ok = true;
+          if (more) {
+            next_ok = mb::test(&full[is], iph) || mb::wait(&full[is], iph, abort_flag, status, kGWaitNs);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
           if (!more) break;
           if (!next_ok) {
             ok = false;

@@ -29,15 +29,21 @@ constexpr uint32_t kNoallocMaxOps = 2 * (kNoallocMaxEvictions + 3) + 2;
 // zero: a move writes the temporary before reading it).
 static __device__ __align__(256) uint8_t g_noalloc_tmp[kNoallocMaxMsgBytes];
 
-struct NoallocMoves {
+// The move list travels in the kernel parameters; the launch copies the whole
+// parameter block, so walks of up to 48 moves (nearly all) take a small one.
+template <uint32_t OPS>
+struct NoallocMovesT {
   uint32_t count;
   uint32_t pad;
-  MoveOp ops[kNoallocMaxOps];
+  MoveOp ops[OPS];
 };
+using NoallocMoves = NoallocMovesT<kNoallocMaxOps>;
+using NoallocMovesS = NoallocMovesT<48>;
 static_assert(sizeof(NoallocMoves) + 64 < 32000, "kernel parameters must stay below 32 KB");
 
+template <typename NM>
 __global__ void __launch_bounds__(256) apply_moves_noalloc_kernel(
-    uint8_t* __restrict__ table, uint32_t z, const __grid_constant__ NoallocMoves m,
+    uint8_t* __restrict__ table, uint32_t z, const __grid_constant__ NM m,
     const uint8_t* __restrict__ msg, uint8_t* __restrict__ tmp) {
   const uint32_t z4 = z / 16;
   for (uint32_t i = 0; i < m.count; ++i) {
@@ -106,10 +112,6 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
     db->meta->rollback(undo);
     return TPIR_EINVAL;
   }
-  NoallocMoves m;
-  m.count = static_cast<uint32_t>(ops.size());
-  m.pad = 0;
-  std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
 
   // after every read already submitted on this db (its own stream included)
   // and after every earlier write to it, whichever stream that ran on
@@ -118,9 +120,22 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, db->stream_mark, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, db->last_write, 0);
   if (e == cudaSuccess) {
-    apply_moves_noalloc_kernel<<<1, 256, 0, st>>>(db->d_table, db->z, m,
-                                                  static_cast<const uint8_t*>(d_msg),
-                                                  static_cast<uint8_t*>(tmp));
+    const uint8_t* msg = static_cast<const uint8_t*>(d_msg);
+    if (ops.size() <= 48) {
+      NoallocMovesS m;
+      m.count = static_cast<uint32_t>(ops.size());
+      m.pad = 0;
+      std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
+      apply_moves_noalloc_kernel<NoallocMovesS><<<1, 256, 0, st>>>(db->d_table, db->z, m, msg,
+                                                                   static_cast<uint8_t*>(tmp));
+    } else {
+      NoallocMoves m;
+      m.count = static_cast<uint32_t>(ops.size());
+      m.pad = 0;
+      std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
+      apply_moves_noalloc_kernel<NoallocMoves><<<1, 256, 0, st>>>(db->d_table, db->z, m, msg,
+                                                                  static_cast<uint8_t*>(tmp));
+    }
     e = cudaGetLastError();
   }
   // the tensor-core read's transposed copy (if the db has one) follows the
