@@ -854,6 +854,392 @@ __global__ void __launch_bounds__(kGThreads, 1)
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// The CTA-pair form (tcgen05 cta_group::2), for one job of more than 128
+// requests.  Two CTAs of a cluster share every MMA: M = 256 requests (128 in
+// each CTA's shared memory) x N = 224 table columns (112 in each CTA's) x K =
+// 64, issued by the even CTA, each CTA's tensor memory holding its 128
+// requests' counts.  A pair item is (two strips = 448 columns, a block of up
+// to 256 requests, a k-chunk): per stage each CTA expands its 128 request
+// rows and 2 x 112 table columns (44 KiB, against 60 KiB for the 256 x 224 of
+// a single CTA) and each MMA reads 7.5 KiB of its shared memory (against 11
+// KiB): the shared-memory traffic per multiply-add that bounds the kernel
+// falls by about 30 %.
+//
+// Per CTA: warp 0 TMA (the CTA's own raw stages), 7 table expanders (warps
+// 1, 5, 9, 13, 3, 7, 11: lane = column 32 i + lane of the CTA's 224, i.e.
+// tile c / 112, column c % 112 of that tile), 4 request expanders (warps 2,
+// 6, 10, 14: lane = request 32 i + lane of the CTA's 128), the MMA thread
+// (warp 24, even CTA only), 8 epilogue warps (16..23: N-tile (w - 16) / 4,
+// lanes 32 (w % 4) ..), warps 4, 8, 12, 15 of the odd CTA relays (idle in
+// the even one).  Every expander warp arrives at its own CTA's "full" barrier
+// of the stage; in the odd CTA relay k (one thread) waits for the barriers of
+// ring slot k and passes one cluster-scope arrival to the even CTA's "pfull"
+// (such an arrival stalls its thread for hundreds of cycles: per expander warp
+// it cost each warp about a thousand cycles a stage, and one relay thread for
+// all slots fell behind), and the MMA thread waits for both.  The MMAs' commits arrive at the "empty"
+// barriers of both CTAs (multicast), their accumulators' at both "accf"
+// barriers; every epilogue warp of both arrives at the even CTA's "acce".
+// All waits bounded; both CTAs meet at a cluster barrier before the tensor
+// memory is freed.
+constexpr int kPCols = 112;                          // table columns per CTA per N-tile
+constexpr int kPTileA = 128 * kGRowBytes;            // 16 KiB: the CTA's 128 request rows
+constexpr int kPTileB = kPCols * kGRowBytes;         // 14 KiB
+constexpr int kPStageBytes = kPTileA + 2 * kPTileB;  // 44 KiB
+constexpr int kPStages = 4;
+constexpr int kPRaw = 4;
+constexpr int kPRawTile = kPCols * kGStageWords * 8;  // 3.5 KiB: a tile's words of a stage
+constexpr int kPRawTable = 2 * kPRawTile;
+template <int RM>
+__host__ __device__ constexpr int p_raw_req() { return RM == 1 ? 128 * 32 : 64 * 32 + 64 * 48; }
+template <int RM>
+__host__ __device__ constexpr int p_raw_bytes() { return kPRawTable + p_raw_req<RM>(); }
+template <int RM>
+__host__ __device__ constexpr int p_smem() { return 1024 + kPStages * kPStageBytes + kPRaw * p_raw_bytes<RM>(); }
+static_assert(p_smem<1>() <= 231424 && p_smem<2>() <= 231424,
+              "dynamic shared memory above 227 KiB less the static part");
+constexpr uint32_t kPTableWarps = 7, kPReqWarps = 4;
+constexpr int kPThreads = 25 * 32;
+constexpr uint64_t kPDescStage = kPStageBytes >> 4;
+constexpr uint64_t kPDescTileB = kPTileB >> 4;
+// M = 256 (bits 24..28 = M / 16), N = 224, e2m1 x e2m1, UE8M0 scales
+constexpr uint32_t kPIdesc = (1u << 7) | (1u << 10) | ((uint32_t)(kGCols >> 3) << 17) | (1u << 23) |
+                             ((256u >> 4) << 24);
+
+__device__ __forceinline__ int p_relay_index(uint32_t warp) {
+  switch (warp) {
+    case 4: return 0; case 8: return 1; case 12: return 2; case 15: return 3;
+    default: return -1;
+  }
+}
+static_assert(kPStages == 4, "one relay warp per ring slot");
+__device__ __forceinline__ int p_req_index(uint32_t warp) {
+  switch (warp) {
+    case 2: return 0; case 6: return 1; case 10: return 2; case 14: return 3;
+    default: return -1;
+  }
+}
+
+__device__ __forceinline__ void p_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t sfa,
+                                      uint32_t sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], "
+      "p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kPIdesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+      : "memory");
+}
+// commit of the MMAs issued so far to the barrier at this offset in both CTAs
+__device__ __forceinline__ void p_commit_both(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], "
+      "%1;" ::"r"(mb::saddr(bar)),
+      "h"(static_cast<uint16_t>(3))
+      : "memory");
+}
+__device__ __forceinline__ void p_commit_self(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   mb::saddr(bar))
+               : "memory");
+}
+
+// Pair items: (pair strip, M-block, k-chunk), pair strip fastest; the pairs
+// take them round by round like the CTAs of the single-CTA kernel.
+struct PItem {
+  uint32_t pstrip, b0;
+  uint64_t k0, k1;
+};
+__device__ __forceinline__ bool p_item(const GJob& J, uint32_t total, uint32_t pair, uint32_t npairs,
+                                       uint32_t r, PItem& it) {
+  const uint32_t c = (r & 1u) ? npairs - 1u - pair : pair;
+  const uint32_t item = c + r * npairs;
+  if (item >= total) return false;
+  const uint32_t nps = (J.n_strips + 1) / 2;
+  it.pstrip = item % nps;
+  const uint32_t rest = item / nps;
+  it.b0 = (rest % J.n_mb) * 256u;
+  it.k0 = static_cast<uint64_t>(rest / J.n_mb) * J.kc_rows;
+  it.k1 = min(J.n, it.k0 + J.kc_rows);
+  return true;
+}
+struct PCursor {
+  uint32_t r;
+  uint64_t ks;
+  PItem it;
+  bool valid;
+};
+__device__ __forceinline__ void p_cur_item(PCursor& c, const GJob& J, uint32_t total, uint32_t pair,
+                                           uint32_t npairs) {
+  c.valid = p_item(J, total, pair, npairs, c.r++, c.it);
+  if (c.valid) c.ks = c.it.k0;
+}
+__device__ __forceinline__ void p_cur_next(PCursor& c, const GJob& J, uint32_t total, uint32_t pair,
+                                           uint32_t npairs) {
+  c.ks += kGKStage;
+  if (c.ks >= c.it.k1) p_cur_item(c, J, total, pair, npairs);
+}
+
+template <int RM>
+__global__ void __launch_bounds__(kPThreads, 1)
+    gf2_mma_pair_kernel(const __grid_constant__ GLaunch<1> L, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[kPStages], pfull[kPStages], empty[kPStages], accf, acce, drain;
+  __shared__ __align__(8) uint64_t raw_full[kPRaw], raw_empty[kPRaw];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  uint8_t* stages = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const uint32_t stage0 = mb::saddr(stages);
+  const uint32_t raw0 = stage0 + kPStages * kPStageBytes;
+  volatile int* abort_flag = &s_abort;
+  constexpr int kRawBytes = p_raw_bytes<RM>();
+  const GJob& J = L.jobs[0];
+  const uint32_t rank = mb::cluster_rank();
+  const uint32_t pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const uint32_t total = L.total_items;
+
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPStages; ++s) {
+      mb::init(&full[s], kPTableWarps + kPReqWarps);  // this CTA's expander warps
+      mb::init(&pfull[s], 1);                         // even CTA: the odd CTA's relay
+      mb::init(&empty[s], 1);
+    }
+    mb::init(&accf, 1);
+    mb::init(&acce, 2 * 8);  // every epilogue warp of both CTAs
+    mb::init(&drain, 1);
+    for (int s = 0; s < kPRaw; ++s) {
+      mb::init(&raw_full[s], 1);
+      mb::init(&raw_empty[s], kPTableWarps + kPReqWarps);
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kGEpiWarp0) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     mb::saddr(&s_tmem)),
+                 "r"(kGTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  mb::cluster_sync();  // both CTAs' barriers initialised, tensor memory allocated
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  if (warp >= kGEpiWarp0 && warp < kGEpiWarp0 + 4) {
+    const uint32_t one = 0x7F7F7F7Fu;  // scale factors 1.0, columns 448..511
+    for (uint32_t col = kGSfCol; col < kGTmemCols; col += 8)
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(
+              tmem + (((warp & 3u) * 32u) << 16) + col),
+          "r"(one)
+          : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  mb::cluster_sync();  // both CTAs' scale factors in place before the first MMA
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t lead_pfull0 = mb::cluster_addr(&pfull[0], 0);
+  const uint32_t lead_acce = mb::cluster_addr(&acce, 0);
+
+  if (warp == kGTmaWarp) {
+    // ------------- this CTA's transposed-table words and request words -------------
+    if (lane == 0) {
+      uint32_t p = 0;
+      PCursor c{};
+      p_cur_item(c, J, total, pair, npairs);
+      for (; c.valid; p_cur_next(c, J, total, pair, npairs), ++p) {
+        const uint32_t rs = p % kPRaw, ph = (p / kPRaw) & 1u;
+        if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
+        const uint32_t dst = raw0 + rs * kRawBytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         mb::saddr(&raw_full[rs])),
+                     "r"(kRawBytes)
+                     : "memory");
+        const int kb = static_cast<int>(c.ks >> 6);
+        const int x0 = static_cast<int>(c.it.pstrip * 2u * kGCols + rank * kPCols);
+        g_tma_load(dst, &L.maps[0], x0, kb, &raw_full[rs]);
+        g_tma_load(dst + kPRawTile, &L.maps[0], x0 + kGCols, kb, &raw_full[rs]);
+        const int b = static_cast<int>(c.it.b0 + 128u * rank);
+        if constexpr (RM == 1) {
+          g_tma_load(dst + kPRawTable, &L.rmaps[0], kb, b, &raw_full[rs]);
+        } else {
+          g_tma_load(dst + kPRawTable, &L.rmaps[0], kb, b >> 1, &raw_full[rs]);
+          g_tma_load(dst + kPRawTable + 64 * 32, &L.rmaps_o[0], static_cast<int>(J.words64) + kb - 1,
+                     b >> 1, &raw_full[rs]);
+        }
+      }
+      for (uint32_t rs = 0; rs < static_cast<uint32_t>(kPRaw) && rs < p; ++rs) {
+        const uint32_t last = rs + kPRaw * ((p - 1 - rs) / kPRaw);
+        const uint64_t t0 = mb::gtimer();
+        while (!mb::try_wait(&raw_full[rs], (last / kPRaw) & 1u)) {
+          if (mb::gtimer() - t0 > kGWaitNs) {
+            atomicExch(status, static_cast<int>(TPIR_ETIMEDOUT));
+            break;
+          }
+        }
+      }
+    }
+  } else if (g_table_index(warp) >= 0 || p_req_index(warp) >= 0) {
+    // ------------------------------ expanders ------------------------------
+    const bool table = g_table_index(warp) >= 0;
+    const uint32_t idx = static_cast<uint32_t>(table ? g_table_index(warp) : p_req_index(warp));
+    const uint32_t e = 32u * idx + lane;  // table column e of the CTA's 224, or request e of its 128
+    const uint32_t t = e >= static_cast<uint32_t>(kPCols) ? 1u : 0u, cc = e - t * kPCols;
+    uint32_t iter = 0;
+    PCursor c{};
+    p_cur_item(c, J, total, pair, npairs);
+    for (; c.valid; p_cur_next(c, J, total, pair, npairs), ++iter) {
+      const uint32_t rs = iter % kPRaw, rph = (iter / kPRaw) & 1u;
+      const uint32_t s = iter % kPStages, ph = (iter / kPStages) & 1u;
+      if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) break;
+      const uint32_t base = raw0 + rs * kRawBytes;
+      uint64_t x[kGStageWords];
+      if (table) {
+#pragma unroll
+        for (int i = 0; i < kGStageWords; ++i)
+          x[i] = ld_shared_u64(base + t * kPRawTile + i * (kPCols * 8) + cc * 8u);
+      } else if constexpr (RM == 1) {
+        const uint32_t a = base + kPRawTable + e * 32u, h = (e >> 2) & 1u;
+        const uint4 v0 = ld_shared_v4(a + 16u * h), v1 = ld_shared_v4(a + 16u * (h ^ 1u));
+        const uint4 lo = h ? v1 : v0, hi = h ? v0 : v1;
+        x[0] = lo.x | static_cast<uint64_t>(lo.y) << 32;
+        x[1] = lo.z | static_cast<uint64_t>(lo.w) << 32;
+        x[2] = hi.x | static_cast<uint64_t>(hi.y) << 32;
+        x[3] = hi.z | static_cast<uint64_t>(hi.w) << 32;
+      } else {
+        const uint32_t pr = e >> 1;
+        const uint32_t a = (e & 1u) ? base + kPRawTable + 64u * 32u + pr * 48u + 8u
+                                    : base + kPRawTable + pr * 32u;
+#pragma unroll
+        for (uint32_t i = 0; i < kGStageWords; ++i) x[i] = ld_shared_u64(a + 8u * i);
+      }
+      {
+        uint32_t used = 0;
+#pragma unroll
+        for (int i = 0; i < kGStageWords; ++i)
+          used ^= static_cast<uint32_t>(x[i]) ^ static_cast<uint32_t>(x[i] >> 32);
+        asm volatile("fence.proxy.async.shared::cta;" ::"r"(used) : "memory");
+        __syncwarp();
+        if (lane == 0) mb::arrive(&raw_empty[rs]);
+      }
+      if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
+      const bool store = table || c.it.b0 + 128u * rank + e < J.B;
+      if (store) {
+        const uint32_t o = table ? stage0 + s * kPStageBytes + kPTileA + t * kPTileB + g_off(cc, 0)
+                                 : stage0 + s * kPStageBytes + g_off(e, 0);
+#pragma unroll
+        for (int i = 0; i < kGStageWords; ++i) {
+          st_shared_v4(o + (2 * i) * kGLbo, g_spread(static_cast<uint32_t>(x[i])));
+          st_shared_v4(o + (2 * i + 1) * kGLbo, g_spread(static_cast<uint32_t>(x[i] >> 32)));
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mb::arrive(&full[s]);
+    }
+  } else if (rank == 1 && p_relay_index(warp) >= 0) {
+    // ---- relays: the odd CTA's stages of ring slot k, one cluster-scope arrival each ----
+    if (lane == 0) {
+      const uint32_t k = static_cast<uint32_t>(p_relay_index(warp));
+      uint32_t iter = 0;
+      PCursor c{};
+      p_cur_item(c, J, total, pair, npairs);
+      for (; c.valid; p_cur_next(c, J, total, pair, npairs), ++iter) {
+        if (iter % kPStages != k) continue;
+        const uint32_t ph = (iter / kPStages) & 1u;
+        if (!mb::wait(&full[k], ph, abort_flag, status, kGWaitNs)) break;
+        mb::arrive_cluster(lead_pfull0 + 8u * k);
+      }
+    }
+  } else if (warp == kGIssueWarp && rank == 0) {
+    // ---------------------- MMA issue for the pair (one thread) ----------------------
+    if (lane == 0) {
+      const uint64_t adesc0 = g_desc(stage0), bdesc0 = g_desc(stage0 + kPTileA);
+      const uint32_t sfa = tmem + kGSfa, sfb = tmem + kGSfb;
+      uint32_t is = 0, iph = 0;
+      for (uint32_t r = 0;; ++r) {
+        PItem it;
+        if (*abort_flag || !p_item(J, total, pair, npairs, r, it)) break;
+        bool ok = true;
+        if (r >= 1) ok = mb::wait_cluster(&acce, (r - 1u) & 1u, abort_flag, status, kGWaitNs);
+        bool have = ok && mb::wait(&full[is], iph, abort_flag, status, kGWaitNs) &&
+                    mb::wait_cluster(&pfull[is], iph, abort_flag, status, kGWaitNs);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ok = have;
+        for (uint64_t ks = it.k0; have; ks += kGKStage) {
+          const uint32_t s = is;
+          if (++is == kPStages) {
+            is = 0;
+            iph ^= 1u;
+          }
+          const bool more = ks + kGKStage < it.k1;
+          const uint64_t sa = adesc0 + s * kPDescStage, sb = bdesc0 + s * kPDescStage;
+          const uint32_t acc0 = ks > it.k0 ? 1u : 0u;
+          const uint64_t left = it.k1 - ks;
+          const uint32_t nk =
+              left >= kGKStage ? 4u : static_cast<uint32_t>((left + kGKStep - 1) / kGKStep);
+          for (uint32_t j = 0; j < nk; ++j)
+#pragma unroll
+            for (uint32_t t = 0; t < 2; ++t)
+              p_mma(tmem + kGCols * t, sa + kDescK * j, sb + kPDescTileB * t + kDescK * j, sfa, sfb,
+                    j ? 1u : acc0);
+          p_commit_both(&empty[s]);
+          if (!more) break;
+          if (!mb::wait(&full[is], iph, abort_flag, status, kGWaitNs) ||
+              !mb::wait_cluster(&pfull[is], iph, abort_flag, status, kGWaitNs)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        if (!ok) break;
+        p_commit_both(&accf);
+      }
+      p_commit_self(&drain);
+      const uint64_t t0 = mb::gtimer();
+      while (!mb::try_wait(&drain, 0)) {
+        if (mb::gtimer() - t0 > kGWaitNs) {
+          atomicExch(status, static_cast<int>(TPIR_ETIMEDOUT));
+          break;
+        }
+      }
+    }
+  } else if (warp >= kGEpiWarp0 && warp < kGEpiWarp0 + 8) {
+    // ---------------- epilogue: this CTA's 128 requests x the item's 2 strips ----------------
+    const uint32_t quarter = warp & 3u, half = (warp - kGEpiWarp0) >> 2;
+    bool pdl_waited = false;
+    for (uint32_t r = 0;; ++r) {
+      PItem it;
+      if (*abort_flag || !p_item(J, total, pair, npairs, r, it)) break;
+      if (!mb::wait_sleep(&accf, r & 1u, abort_flag, status, kGWaitNs, 256)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!pdl_waited) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");  // replies initialised / released
+        pdl_waited = true;
+      }
+      const uint32_t lanes = (32u * quarter) << 16;
+      g_epilogue(J, tmem + lanes + kGCols * half, it.b0 + 128u * rank + 32u * quarter + lane,
+                 (2u * it.pstrip + half) * kGStripWords, kGStripWords);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mb::arrive_cluster(lead_acce);
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  mb::cluster_sync();  // the pair's MMAs are complete before either CTA frees its memory
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == kGEpiWarp0)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kGTmemCols)
+                 : "memory");
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encoder() {
   static std::mutex mu;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -870,15 +1256,16 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encoder() {
 }
 
 // Tensor map of a transposed table as a 2-D array of 64-bit words (row_bits
-// columns x ceil(n / 64) blocks), box 224 columns x 4 blocks; encoded once
-// per (copy, shape).
-cudaError_t g_table_map(const uint64_t* Tt, uint64_t n, uint32_t Wd, CUtensorMap* out) {
+// columns x ceil(n / 64) blocks), box `width` columns (224, or 112 for a CTA
+// of a pair) x 4 blocks; encoded once per (copy, shape, box).
+cudaError_t g_table_map(const uint64_t* Tt, uint64_t n, uint32_t Wd, CUtensorMap* out,
+                        uint32_t width = kGCols) {
   static std::mutex mu;
-  static std::map<std::tuple<const void*, uint64_t, uint32_t>, CUtensorMap> cache;
+  static std::map<std::tuple<const void*, uint64_t, uint32_t, uint32_t>, CUtensorMap> cache;
   PFN_cuTensorMapEncodeTiled_v12000 encode = g_encoder();
   if (!encode) return cudaErrorNotSupported;
   std::lock_guard<std::mutex> g(mu);
-  const auto key = std::make_tuple(static_cast<const void*>(Tt), n, Wd);
+  const auto key = std::make_tuple(static_cast<const void*>(Tt), n, Wd, width);
   const auto it = cache.find(key);
   if (it != cache.end()) {
     *out = it->second;
@@ -888,7 +1275,7 @@ cudaError_t g_table_map(const uint64_t* Tt, uint64_t n, uint32_t Wd, CUtensorMap
   const uint64_t row_bits = static_cast<uint64_t>(Wd) * 32;
   const cuuint64_t dims[2] = {row_bits, (n + 63) / 64};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(row_bits) * 8};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kGCols), static_cast<cuuint32_t>(kGStageWords)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(width), static_cast<cuuint32_t>(kGStageWords)};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(Tt), dims,
                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1019,6 +1406,108 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
   return launch_pdl(gf2_mma_kernel<NJ, RM>, dim3(grid), dim3(kGThreads), g_smem<RM>(), st, L, status);
 }
 
+// Pairs a launch of the pair kernel can hold resident at once (clusters of
+// two CTAs of one SM each), once per request-staging mode.
+template <int RM>
+int p_max_pairs() {
+  static std::atomic<int> cached{0};
+  int v = cached.load(std::memory_order_acquire);
+  if (v) return v;
+  cudaError_t e = cudaFuncSetAttribute(gf2_mma_pair_kernel<RM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, p_smem<RM>());
+  if (e != cudaSuccess) return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(device_sm_count() & ~1));
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = p_smem<RM>();
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&clusters, gf2_mma_pair_kernel<RM>, &cfg);
+  if (e != cudaSuccess || clusters <= 0) return -1;
+  cached.store(clusters, std::memory_order_release);
+  return clusters;
+}
+
+// One job on CTA pairs (B > 128, request rows TMA-staged): items of whole
+// k-chunks taken round by round, k-chunks chosen like the single-CTA item
+// schedule (about 119 cycles per pair MMA, two per K-step).
+template <int RM>
+cudaError_t g_launch_pair(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uint64_t* R,
+                          uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
+                          cudaStream_t st, const GSched* sched) {
+  const int pairs = p_max_pairs<RM>();
+  if (pairs <= 0) return cudaErrorNotSupported;
+  int* status = device_status_word();
+  if (!status) return cudaErrorInvalidSymbol;
+  GLaunch<1> L{};
+  L.njobs = 1;
+  L.nbuf = 1;
+  GJob J = g_job(R, words64, B, out, seeds, n, Wd);
+  const uint64_t nps = (J.n_strips + 1) / 2;
+  const uint64_t max_kc = std::max<uint64_t>(1, (n + kGKStage - 1) / kGKStage);
+  const uint64_t min_kc = (n + kGMaxCount - 1) / kGMaxCount;
+  double best = 1e300;
+  uint64_t best_rows = kGKStage;
+  for (uint64_t c = std::max<uint64_t>(1, min_kc);
+       c <= std::max<uint64_t>(min_kc, std::min<uint64_t>(max_kc, 512)); ++c) {
+    const uint64_t rows = g_clamp_rows((n + c - 1) / c, n);
+    const uint64_t kcs = (n + rows - 1) / rows;
+    const uint64_t items = nps * J.n_mb * kcs;
+    const uint64_t rounds = (items + pairs - 1) / pairs;
+    const double cost = static_cast<double>(rounds) *
+                        (static_cast<double>(rows) / kGKStep * 2.0 * 119.0 + 3000.0);
+    if (cost < best) {
+      best = cost;
+      best_rows = rows;
+    }
+  }
+  J.kc_rows = static_cast<uint32_t>(best_rows);
+  if (sched && sched->mode == 2 && sched->kc_rows) J.kc_rows = g_clamp_rows(sched->kc_rows, n);
+  const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;
+  const uint64_t items = nps * J.n_mb * kcs;
+  if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  J.split = kcs > 1 ? 1u : seeds ? 2u : 0u;
+  J.item_begin = 0;
+  const uint64_t nw = (n + 63) / 64;
+  if (RM == 1) {
+    if (g_req_map(R, nw, B, words64, kGStageWords, 128, &L.rmaps[0]) != cudaSuccess)
+      return cudaErrorInvalidValue;
+  } else {
+    if (g_req_map(R, nw, (B + 1) / 2, 2ull * words64, kGStageWords, 64, &L.rmaps[0]) != cudaSuccess ||
+        g_req_map(R, words64 + nw, B / 2, 2ull * words64, kGStageWords + 2, 64, &L.rmaps_o[0]) !=
+            cudaSuccess)
+      return cudaErrorInvalidValue;
+  }
+  J.req_tma = RM;
+  L.jobs[0] = J;
+  L.total_items = static_cast<uint32_t>(items);
+  cudaError_t e = g_table_map(Tt, n, Wd, &L.maps[0], kPCols);
+  if (e != cudaSuccess) return e;
+  if (J.split == 1) e = launch_pdl(gf2_init_kernel<1>, dim3(64, 1), dim3(256), 0, st, L);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * std::min<uint64_t>(items, pairs)));
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = p_smem<RM>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, gf2_mma_pair_kernel<RM>, L, status);
+}
+
 }  // namespace
 
 bool gf2_span_ok(uint64_t n, uint32_t Wd, uint32_t B) {
@@ -1032,6 +1521,13 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
                            uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                            cudaStream_t st, const GSched* sched) {
   if (B == 0) return cudaSuccess;
+  // more than one M-tile of requests whose rows TMA can stage: CTA pairs
+  // (unless a schedule asks for spans or per-thread request loads)
+  if (B > 128 && !(sched && (sched->mode == 1 || sched->loads))) {
+    const uint32_t rm = g_req_mode(R, words64);
+    if (rm == 1) return g_launch_pair<1>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
+    if (rm == 2) return g_launch_pair<2>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
+  }
   GLaunch<1> L{};
   L.njobs = 1;
   GJob J = g_job(R, words64, B, out, seeds, n, Wd);
@@ -1168,13 +1664,28 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode,
 
 cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
   if (count > TPIR_MAX_JOBS) return cudaErrorInvalidValue;
-  // jobs grouped by how TMA stages their request words (rows, row pairs,
-  // per-thread loads), in launches of at most kGMultiJobs jobs (the kernel
-  // parameters hold three tensor maps per job), in stream order
+  // Jobs of more than 128 requests whose rows TMA can stage run on CTA pairs,
+  // one launch each (a pair launch holds one job); the others are grouped by
+  // how TMA stages their request words (rows, row pairs, per-thread loads),
+  // in launches of at most kGMultiJobs jobs (the kernel parameters hold three
+  // tensor maps per job), in stream order.
+  auto paired = [](const M4Request& q) {
+    return q.B > 128 && !q.loads && g_req_mode(q.R, q.words64) != 0;
+  };
+  for (uint32_t i = 0; i < count; ++i) {
+    const M4Request& q = reqs[i];
+    if (!q.B || !paired(q)) continue;
+    if (!q.Tt) return cudaErrorInvalidValue;
+    const GSched sched{2u, q.kc_rows, 0u};
+    const cudaError_t e = launch_gf2_mma(q.Tt, q.n, q.Wd, q.R, q.words64, q.B, q.out, q.seeds, st,
+                                         q.kc_rows ? &sched : nullptr);
+    if (e != cudaSuccess) return e;
+  }
   for (uint32_t mode : {1u, 2u, 0u}) {
     std::vector<M4Request> part;
     for (uint32_t i = 0; i < count; ++i)
-      if (reqs[i].B && (reqs[i].loads ? 0u : g_req_mode(reqs[i].R, reqs[i].words64)) == mode)
+      if (reqs[i].B && !paired(reqs[i]) &&
+          (reqs[i].loads ? 0u : g_req_mode(reqs[i].R, reqs[i].words64)) == mode)
         part.push_back(reqs[i]);
     for (size_t i = 0; i < part.size(); i += kGMultiJobs) {
       const uint32_t c = static_cast<uint32_t>(std::min<size_t>(kGMultiJobs, part.size() - i));
