@@ -53,8 +53,8 @@ TRAFFIC_BATCHED_B256 = (136.659968e6 + 3.284480e6 + 136.435200e6 + 0.130304e6 + 
 TRAFFIC_PLAIN_B1 = 134.240768e6 + 3.548928e6
 TRAFFIC_M4RM_B256 = (136.340736e6 + 3.074048e6 + 136.585216e6 + 0.072192e6 + 136.370944e6
                      + 0.116480e6) / 3
-TRAFFIC_GF2MMA_B256 = (135.352320e6 + 2.965248e6 + 135.358208e6 + 0.170496e6 + 135.383296e6
-                       + 0.146176e6) / 3
+TRAFFIC_GF2MMA_B256 = (135.351040e6 + 2.960640e6 + 135.359488e6 + 0.532736e6 + 135.379200e6
+                       + 0.106752e6) / 3
 
 
 def measured_peaks() -> dict:
@@ -79,7 +79,7 @@ def m4rm_smem_bytes(n: int, row_words: int, B: int) -> float:
     return float(groups) * wtiles * (btiles * 256 * 64 * 4 + B * 64 * 4)
 
 
-FP4_ISSUE_PFLOPS_2070 = 9.44  # tcgen05.mma kind::mxf4, M=128 x N=224 x K=64, all SMs at 2070 MHz
+FP4_ISSUE_PFLOPS_2070 = 9.70  # tcgen05.mma kind::mxf4 N=224 K=64, M=128 or a CTA pair's M=256, all SMs at 2070 MHz (tests/test_gpu_mma_rates.py)
 
 
 def fp4_peak_tflops(peaks: dict) -> tuple[float, str]:
@@ -502,10 +502,10 @@ def main() -> None:
             "roofline": {"bound": "tensor", "achieved": tc_tflops, "peak": tc_peak,
                          "unit": "TFLOP/s", "frac": tc_tflops / tc_peak,
                          "traffic": TRAFFIC_GF2MMA_B256,
-                         "kernel": "gf2_mma_kernel (tcgen05 kind::mxf4, e2m1 0/1 operands)",
+                         "kernel": "gf2_mma_pair_kernel (tcgen05 cta_group::2 kind::mxf4, e2m1 0/1 operands)",
                          "peak_basis": tc_basis,
                          "frac_of_issue_rate": tc_tflops / (FP4_ISSUE_PFLOPS_2070 * 1e3 * sm_mhz / 2070.0),
-                         "issue_rate_basis": "back-to-back kind::mxf4 M=128 N=224 K=64 MMAs on all SMs (9.44 PFLOP/s at 2070 MHz), scaled to the sampled clock",
+                         "issue_rate_basis": "back-to-back kind::mxf4 N=224 K=64 MMAs (M=128 per SM, or M=256 per CTA pair) on all SMs, 9.70 PFLOP/s at 2070 MHz (tests/test_gpu_mma_rates.py), scaled to the sampled clock",
                          "lop3_equivalent_tops": ops_per_launch / (launch_ms * 1e-3) / 1e12},
             "head_m4rm": m4,
             "head_lop3": lop3,
