@@ -258,7 +258,8 @@ typedef struct {
     double us_per_launch;      /* of the chosen register-tiled shape */
     double lop3_tops;          /* B*n*row_words / time */
     uint32_t kernel;           /* fastest kernel (as in tpir_db_set_kernel) */
-    uint32_t tensor_mode;      /* its tensor-core schedule: 1 spans, 2 items */
+    uint32_t tensor_mode;      /* its tensor-core schedule: 1 spans, 2 items (on CTA pairs above
+                                  128 requests), 3 items on single CTAs */
     uint32_t tensor_kc_rows;   /* items: k-chunk buckets (0: planned size) */
     uint32_t tensor_loads;     /* 1: request words loaded by threads, not TMA */
     uint32_t tensor_candidates;

@@ -1522,8 +1522,9 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
                            cudaStream_t st, const GSched* sched) {
   if (B == 0) return cudaSuccess;
   // more than one M-tile of requests whose rows TMA can stage: CTA pairs
-  // (unless a schedule asks for spans or per-thread request loads)
-  if (B > 128 && !(sched && (sched->mode == 1 || sched->loads))) {
+  // (unless a schedule asks for spans, single-CTA items or per-thread
+  // request loads)
+  if (B > 128 && !(sched && (sched->mode == 1 || sched->mode == 3 || sched->loads))) {
     const uint32_t rm = g_req_mode(R, words64);
     if (rm == 1) return g_launch_pair<1>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
     if (rm == 2) return g_launch_pair<2>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
@@ -1567,7 +1568,7 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
   // equal spans would (within 10 %), else spans (when admissible).
   bool use_span = span_ok;
   if (mode == 1) use_span = span_ok;
-  else if (mode == 2) use_span = false;
+  else if (mode == 2 || mode == 3) use_span = false;
   else if (span_ok)
     use_span = static_cast<double>(best_rounds * ((best_rows + kGKStage - 1) / kGKStage)) >
                1.1 * static_cast<double>(per_cta);
@@ -1581,7 +1582,7 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
     L.total_items = 0;
   } else {
     J.kc_rows = static_cast<uint32_t>(best_rows);
-    if (mode == 2 && sched->kc_rows) J.kc_rows = g_clamp_rows(sched->kc_rows, n);
+    if ((mode == 2 || mode == 3) && sched->kc_rows) J.kc_rows = g_clamp_rows(sched->kc_rows, n);
     const uint64_t kcs = (n + J.kc_rows - 1) / J.kc_rows;
     const uint64_t items = static_cast<uint64_t>(J.n_strips) * J.n_mb * kcs;
     if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;

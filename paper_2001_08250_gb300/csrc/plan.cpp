@@ -191,6 +191,11 @@ tpir_status tpir_autotune(tpir_db* db, uint32_t B, uint32_t reps, tpir_tune_resu
       for (uint32_t kc : {4096u, 8192u, 16384u, 32768u})
         if (kc < (db->n + 255) / 256 * 256) scheds.push_back(GSched{2, kc, loads});
     }
+    if (B > 128) {  // items on CTA pairs (mode 2 above) against items on single CTAs
+      scheds.push_back(GSched{3, 0, 0});
+      for (uint32_t kc : {4096u, 8192u, 16384u, 32768u})
+        if (kc < (db->n + 255) / 256 * 256) scheds.push_back(GSched{3, kc, 0});
+    }
     for (const GSched& sc : scheds) {
       const double us = time_it([&]() {
         cudaError_t x = tcopy_ensure(db, st);
@@ -325,7 +330,7 @@ tpir_status tpir_tune_load(const char* path) {
                     "\"tensor_mode\": %u, \"tensor_kc_rows\": %u, \"tensor_loads\": %u",
                     &wd, &bc, &nc, &kern, &tm, &kc, &tl) == 7) {
       // accept only choices the library can run
-      if (!(kern == 1 || kern == 2 || kern == 4 || kern == 5) || tm > 2 || wd == 0 || (wd % 4) != 0 ||
+      if (!(kern == 1 || kern == 2 || kern == 4 || kern == 5) || tm > 3 || wd == 0 || (wd % 4) != 0 ||
           (kern >= 4 && wd < 64) || kc > 32768 || (kc % 256) != 0 || tl > 1) {
         rc = TPIR_EINVAL;
         continue;

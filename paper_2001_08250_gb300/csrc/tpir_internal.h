@@ -82,12 +82,13 @@ static_assert(sizeof(ScanLaunch) <= 32000, "kernel parameters must stay below 32
 // Assigns the next item-counter slot (rotating).
 uint32_t next_counter_slot();
 
-// Schedule of a one-table tensor-core launch: mode 0 = planned (spans when
-// every CTA gets at most one k-chunk of stages, else items of k-chunks sized
-// by the cost model), 1 = spans (if admissible), 2 = items of kc_rows buckets
-// (0: the cost model's size); loads = 1: request words loaded by the
+// Schedule of a one-table tensor-core launch: mode 0 = planned (above 128
+// requests with TMA-staged rows: items on CTA pairs; else spans or items as
+// the cost model finds), 1 = spans (if admissible), 2 = items of kc_rows
+// buckets (0: the cost model's size; on CTA pairs above 128 requests), 3 =
+// the same items on single CTAs; loads = 1: request words loaded by the
 // expander threads instead of staged by TMA (room for a deeper ring of table
-// stages).
+// stages; single CTAs).
 struct GSched {
   uint32_t mode = 0;
   uint32_t kc_rows = 0;

@@ -95,3 +95,35 @@ def test_tuned_plans_round_trip_through_json(tmp_path):
     empty = tmp_path / "empty.json"
     talekpir.tune_save(str(empty))
     assert '"row_words"' not in empty.read_text()
+
+
+def test_kernel_plans_round_trip_and_refuse_unknown_schedules(tmp_path):
+    """Kernel plans (the measured winner per table class) load and save with
+    their tensor-core schedule: spans (1), items on CTA pairs (2), items on
+    single CTAs (3); an unknown schedule or kernel is refused."""
+    from paper_2001_08250_gb300 import talekpir
+    import pytest
+    good = tmp_path / "kplans.json"
+    good.write_text(
+        '{"plans": [\n'
+        '{"row_words": 1024, "batch_class": 8, "n_class": 15, "kernel": 5, "tensor_mode": 3, '
+        '"tensor_kc_rows": 16384, "tensor_loads": 0},\n'
+        '{"row_words": 64, "batch_class": 6, "n_class": 12, "kernel": 5, "tensor_mode": 1, '
+        '"tensor_kc_rows": 0, "tensor_loads": 1}\n'
+        ']}\n')
+    talekpir.tune_clear()
+    try:
+        talekpir.tune_load(str(good))
+        out = tmp_path / "out.json"
+        talekpir.tune_save(str(out))
+        text = out.read_text()
+        assert '"tensor_mode": 3, "tensor_kc_rows": 16384, "tensor_loads": 0' in text
+        assert '"tensor_mode": 1, "tensor_kc_rows": 0, "tensor_loads": 1' in text
+        for bad_plan in ('"kernel": 5, "tensor_mode": 4', '"kernel": 3, "tensor_mode": 0'):
+            bad = tmp_path / "bad.json"
+            bad.write_text('{"plans": [\n{"row_words": 64, "batch_class": 6, "n_class": 12, %s, '
+                           '"tensor_kc_rows": 0, "tensor_loads": 0}\n]}\n' % bad_plan)
+            with pytest.raises(talekpir.TpirError):
+                talekpir.tune_load(str(bad))
+    finally:
+        talekpir.tune_clear()

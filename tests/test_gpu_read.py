@@ -291,16 +291,17 @@ def test_multi_table_large_batches_bit_exact():
     assert talekpir.device_status() == talekpir.OK
 
 
-@pytest.mark.parametrize("n,B,loads", [(32768, 128, 0), (32767, 256, 0), (65536, 200, 1),
-                                       (32768, 64, 1)])
-def test_tensor_kernel_counts_at_the_chunk_bound(n, B, loads, tmp_path):
+@pytest.mark.parametrize("n,B,loads,mode", [(32768, 128, 0, 2), (32767, 256, 0, 2), (32768, 256, 0, 3),
+                                            (65536, 300, 0, 2), (65536, 200, 1, 2), (32768, 64, 1, 2)])
+def test_tensor_kernel_counts_at_the_chunk_bound(n, B, loads, mode, tmp_path):
     """One accumulator over a whole k-chunk of 32 768 buckets: a tuning plan
     (loaded as a user would) makes the tensor-core read take items of whole
-    32 768-bucket k-chunks, and all-ones requests then drive each count to
-    its largest values: 32 767 (odd: a column set on every row but one, or
-    every row of a 32 767-bucket table) and 32 768 (even), besides counts of
-    16 384 and 10 923 (rows k odd, rows k = 0 mod 3).  With 65 536 buckets two
-    full chunks are XOR-combined.  Every reply bit-exact."""
+    32 768-bucket k-chunks (mode 2: on CTA pairs above 128 requests with
+    TMA-staged rows; mode 3: on single CTAs), and all-ones requests then drive
+    each count to its largest values: 32 767 (odd: a column set on every row
+    but one, or every row of a 32 767-bucket table) and 32 768 (even),
+    besides counts of 16 384 and 10 923 (rows k odd, rows k = 0 mod 3).  With
+    65 536 buckets two full chunks are XOR-combined.  Every reply bit-exact."""
     require_cuda()
     d, z = 1, 256                       # 64 words: a row width plans may steer
     T = np.zeros((n, d * z), dtype=np.uint8)
@@ -314,8 +315,8 @@ def test_tensor_kernel_counts_at_the_chunk_bound(n, B, loads, tmp_path):
     nclass = max(0, (n - 1).bit_length())
     plan = tmp_path / "plan.json"
     plan.write_text('{"plans": [\n{"row_words": 64, "batch_class": %d, "n_class": %d, "kernel": 5, '
-                    '"tensor_mode": 2, "tensor_kc_rows": 32768, "tensor_loads": %d}\n]}\n'
-                    % (bclass, nclass, loads))
+                    '"tensor_mode": %d, "tensor_kc_rows": 32768, "tensor_loads": %d}\n]}\n'
+                    % (bclass, nclass, mode, loads))
     talekpir.tune_load(str(plan))
     try:
         exp = oracle.read(T, n, d, z, R[0])
