@@ -1665,13 +1665,17 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode,
 
 cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
   if (count > TPIR_MAX_JOBS) return cudaErrorInvalidValue;
-  // Jobs of more than 128 requests whose rows TMA can stage run on CTA pairs,
-  // one launch each (a pair launch holds one job); the others are grouped by
-  // how TMA stages their request words (rows, row pairs, per-thread loads),
-  // in launches of at most kGMultiJobs jobs (the kernel parameters hold three
-  // tensor maps per job), in stream order.
+  // Jobs of more than 128 requests whose rows TMA can stage, on tables of at
+  // least kPairMinN buckets, run on CTA pairs, one launch each (a pair launch
+  // holds one job; on smaller tables its fixed cost outweighs the gain: the
+  // 64-table benchmark took 16.4 ms with this bound, 16.6 ms pairing every
+  // such job, 17.7 ms pairing none); the others are grouped by how TMA stages
+  // their request words (rows, row pairs, per-thread loads), in launches of
+  // at most kGMultiJobs jobs (the kernel parameters hold three tensor maps
+  // per job), in stream order.
+  constexpr uint64_t kPairMinN = 8192;
   auto paired = [](const M4Request& q) {
-    return q.B > 128 && !q.loads && g_req_mode(q.R, q.words64) != 0;
+    return q.B > 128 && !q.loads && g_req_mode(q.R, q.words64) != 0 && q.n >= kPairMinN;
   };
   for (uint32_t i = 0; i < count; ++i) {
     const M4Request& q = reqs[i];
