@@ -1524,10 +1524,13 @@ cudaError_t launch_gf2_mma(const uint64_t* Tt, uint64_t n, uint32_t Wd, const ui
   // more than one M-tile of requests whose rows TMA can stage: CTA pairs
   // (unless a schedule asks for spans, single-CTA items or per-thread
   // request loads)
+  // (a device that cannot hold the pair kernel's clusters takes single CTAs)
   if (B > 128 && !(sched && (sched->mode == 1 || sched->mode == 3 || sched->loads))) {
     const uint32_t rm = g_req_mode(R, words64);
-    if (rm == 1) return g_launch_pair<1>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
-    if (rm == 2) return g_launch_pair<2>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
+    cudaError_t e = cudaErrorNotSupported;
+    if (rm == 1) e = g_launch_pair<1>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
+    if (rm == 2) e = g_launch_pair<2>(Tt, n, Wd, R, words64, B, out, seeds, st, sched);
+    if (e != cudaErrorNotSupported) return e;
   }
   GLaunch<1> L{};
   L.njobs = 1;
