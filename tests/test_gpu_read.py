@@ -425,3 +425,35 @@ def test_pipelined_host_reads_bit_exact(B_total, batch, kernel):
         # pageable buffers give the same replies (the copies just do not overlap)
         assert np.array_equal(db.read_batch_pipelined(R, batch), got)
     assert talekpir.device_status() == talekpir.OK
+
+
+def test_pipelined_reads_of_several_tables_from_several_threads():
+    """One host thread per table (each thread the only user of its db, as the
+    API allows): concurrent pipelined host-buffer reads of three tables of
+    different shapes, batches that take the CTA-pair tensor-core kernel, the
+    single-CTA one and the plain stream; every reply equals the oracle's."""
+    torch = require_cuda()
+    from concurrent.futures import ThreadPoolExecutor
+    shapes = [(3000, 4, 1024, 700, 256), (2049, 2, 512, 390, 100), (5000, 1, 256, 65, 3)]
+    dbs, jobs = [], []
+    for i, (n, d, z, Bt, batch) in enumerate(shapes):
+        T = synth.table_bytes(n, d, z, seed=120, table=i)
+        R = synth.random_bits(Bt, n, seed=121, table=i)
+        hR = torch.from_numpy(R.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        hO = torch.empty((Bt, d * z), dtype=torch.uint8).pin_memory().numpy()
+        db = _db(n, d, z, T)
+        dbs.append(db)
+        jobs.append((db, hR, hO, batch, oracle.read_batch(T, n, d, z, R)))
+    try:
+        def run(job):
+            db, hR, hO, batch, _ = job
+            for _ in range(3):
+                db.read_batch_pipelined(hR, batch, hO)
+        with ThreadPoolExecutor(len(jobs)) as ex:
+            list(ex.map(run, jobs))
+        for db, hR, hO, batch, exp in jobs:
+            assert np.array_equal(hO, exp), (db.n, batch)
+    finally:
+        for db in dbs:
+            db.close()
+    assert talekpir.device_status() == talekpir.OK
