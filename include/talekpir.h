@@ -226,7 +226,10 @@ tpir_status tpir_xor_combine(const void *const *d_srcs, uint32_t count, uint64_t
  * shared memory, one lookup per request and group), 5 = batched tensor-core
  * kernel (the GF(2) product as an exact integer product of 0/1 matrices on
  * tcgen05: packed 4-bit e2m1 operands with unit block scales, fp32
- * accumulators, reduced mod 2).  The tensor-core kernel reads a
+ * accumulators, reduced mod 2; batches of more than 128 requests run on
+ * pairs of SMs sharing each M = 256 MMA, cta_group::2, unless a tuning plan
+ * chose single CTAs; a device that cannot hold the pairs' clusters takes
+ * single CTAs).  The tensor-core kernel reads a
  * bit-transposed copy of the table (each column's bits over 64 buckets in
  * one word; as large as the table), allocated and built by the first read
  * that uses it and then kept equal to the table by every write and load. */
@@ -239,8 +242,9 @@ tpir_status tpir_db_set_kernel(tpir_db *db, int kernel);
  *     width and the row tile width, and the rows per pipeline stage);
  *   - the tensor-core kernel's schedules (equal spans of stages per CTA, or
  *     items of whole k-chunks of 4096 .. 32768 buckets or the planned size;
- *     request words staged by TMA or loaded by the expander threads) when
- *     rows are 256 bytes or wider;
+ *     request words staged by TMA or loaded by the expander threads; above
+ *     128 requests items on CTA pairs and on single CTAs) when rows are 256
+ *     bytes or wider;
  *   - the Four-Russians kernel (B >= 32, rows of 256 bytes or more) and the
  *     plain kernel (B <= 16);
  * and keeps (a) the fastest tile shape for every later launch of the
@@ -275,7 +279,9 @@ tpir_status tpir_tune_clear(void);
 /* Many tables in ONE persistent launch per kernel kind (the uneven-batching
  * workload): job i reads B_i rows of d_req_bits_i against db_i into d_out_i.
  * Tables may differ in n, d and msg_bytes.  Jobs of >= 48 requests on rows of
- * >= 256 bytes share one launch of the tensor-core kernel, the others one
+ * >= 256 bytes go to the tensor-core kernel: those of more than 128 requests
+ * on tables of >= 8192 buckets one CTA-pair launch each, the rest share one
+ * launch (per request-staging mode), the others one
  * launch of the register-tiled kernel (a db forced to kernel 4 sends its jobs
  * to the Four-Russians kernel instead: one launch for jobs of up to 256
  * requests, one for larger ones; forced to 2, to the register-tiled one).  A
