@@ -320,6 +320,12 @@ tpir_status tpir_selftest_wait_timeout(uint32_t limit_us);
  * device. */
 tpir_status tpir_device_status(void);
 
+/* Kernel launches the library has enqueued in this process so far, of every
+ * kind (reads, reply initialisation, writes, transposed-copy upkeep, interest
+ * vectors, compression); the difference of two calls counts the launches
+ * made between them.  Does not synchronise. */
+uint64_t tpir_kernel_launches(void);
+
 /* ---- private notifications (Section 7) ----------------------------------
  * The global interest vector of a db: m_bits bits, k positions per write, the
  * OR of the `window` most recent deltas; each delta summarises

@@ -921,6 +921,8 @@ tpir_status tpir_device_status(void) {
   return st ? static_cast<tpir_status>(st) : TPIR_OK;
 }
 
+uint64_t tpir_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
+
 // ---- Bloom -----------------------------------------------------------------
 tpir_status tpir_bloom_create(tpir_db* db, uint64_t m_bits, uint32_t k, uint32_t window,
                               uint32_t writes_per_delta) {

@@ -1505,7 +1505,9 @@ cudaError_t g_launch_pair(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uin
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, gf2_mma_pair_kernel<RM>, L, status);
+  e = cudaLaunchKernelEx(&cfg, gf2_mma_pair_kernel<RM>, L, status);
+  if (e == cudaSuccess) count_launches();
+  return e;
 }
 
 }  // namespace

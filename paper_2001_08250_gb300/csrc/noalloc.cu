@@ -128,6 +128,7 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
       std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
       apply_moves_noalloc_kernel<NoallocMovesS><<<1, 256, 0, st>>>(db->d_table, db->z, m, msg,
                                                                    static_cast<uint8_t*>(tmp));
+      count_launches();
     } else {
       NoallocMoves m;
       m.count = static_cast<uint32_t>(ops.size());
@@ -135,6 +136,7 @@ extern "C" tpir_status tpir_write_noalloc(tpir_db* db, uint64_t b1, uint64_t b2,
       std::memcpy(m.ops, ops.data(), ops.size() * sizeof(MoveOp));
       apply_moves_noalloc_kernel<NoallocMoves><<<1, 256, 0, st>>>(db->d_table, db->z, m, msg,
                                                                   static_cast<uint8_t*>(tmp));
+      count_launches();
     }
     e = cudaGetLastError();
   }

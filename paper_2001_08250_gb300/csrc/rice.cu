@@ -264,6 +264,7 @@ cudaError_t launch_rice_encode(const RiceRequest& q, void* scratch, cudaStream_t
   rice_block_kernel<<<static_cast<uint32_t>(nb), kRThreads, 0, st>>>(J, blocks);
   rice_scan_kernel<<<1, kRThreads, 0, st>>>(J, blocks, static_cast<uint32_t>(nb));
   rice_write_kernel<<<static_cast<uint32_t>(nb), kRThreads, 0, st>>>(J, blocks);
+  count_launches(4);
   return cudaGetLastError();
 }
 

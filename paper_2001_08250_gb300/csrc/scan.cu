@@ -753,6 +753,7 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns) {
 
 cudaError_t launch_selftest_wait(uint64_t limit_ns, cudaStream_t st) {
   selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns);
+  count_launches();
   return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ cudaError_t launch_apply_moves(uint8_t* table, uint32_t z, const MoveOp* ops, ui
                                const uint8_t* payloads, uint8_t* tmp, cudaStream_t st) {
   if (nops == 0) return cudaSuccess;
   apply_moves_kernel<<<1, 256, 0, st>>>(table, z, ops, nops, payloads, tmp);
+  count_launches();
   return cudaGetLastError();
 }
 
@@ -102,6 +103,7 @@ cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMove
                                      cudaStream_t st) {
   if (m.nops == 0) return cudaSuccess;
   apply_moves_param_kernel<ParamMoves><<<1, 256, 0, st>>>(table, z, m, tmp);
+  count_launches();
   return cudaGetLastError();
 }
 
@@ -109,6 +111,7 @@ cudaError_t launch_apply_moves_param(uint8_t* table, uint32_t z, const ParamMove
                                      cudaStream_t st) {
   if (m.nops == 0) return cudaSuccess;
   apply_moves_param_kernel<ParamMovesS><<<1, 256, 0, st>>>(table, z, m, tmp);
+  count_launches();
   return cudaGetLastError();
 }
 
@@ -118,6 +121,7 @@ cudaError_t launch_bloom_set(uint64_t* delta, const uint64_t* pos, uint64_t coun
   const uint64_t blocks = (count + 255) / 256;
   bloom_set_kernel<<<static_cast<uint32_t>(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(delta, pos,
                                                                                         count);
+  count_launches();
   return cudaGetLastError();
 }
 
@@ -126,6 +130,7 @@ cudaError_t launch_bloom_or(uint64_t* delta, const uint64_t* vec, uint64_t m, cu
   const uint64_t blocks = (words + 255) / 256;
   bloom_or_kernel<<<static_cast<uint32_t>(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(delta, vec,
                                                                                        m);
+  count_launches();
   return cudaGetLastError();
 }
 
@@ -134,6 +139,7 @@ cudaError_t launch_bloom_union(const uint64_t* deltas, uint32_t window, uint64_t
   const uint64_t blocks = (words + 255) / 256;
   bloom_union_kernel<<<static_cast<uint32_t>(blocks < 1024 ? blocks : 1024), 256, 0, st>>>(
       deltas, window, words, out);
+  count_launches();
   return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ cudaError_t launch_tcopy(const tpir_db* db, const TcopyBlocks& bl, cudaStream_t 
   const uint64_t grid = std::min<uint64_t>(items, static_cast<uint64_t>(device_sm_count()) * 8);
   tcopy_kernel<<<static_cast<uint32_t>(grid), 256, 0, st>>>(
       reinterpret_cast<const uint32_t*>(db->d_table), db->n, db->Wd, db->d_tt, nblocks, bl);
+  count_launches();
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -115,6 +116,11 @@ int scan_stage_bytes(const Shape& s);
 // Launch with programmatic dependent launch (PDL) allowed: the kernel may
 // start while the previous kernel of the stream runs; it must execute
 // griddepcontrol.wait before touching anything that kernel writes.
+// Kernel launches the library has enqueued in this process (every kind);
+// tpir_kernel_launches() returns it.
+inline std::atomic<uint64_t> g_kernel_launches{0};
+inline void count_launches(uint64_t k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t st, Args... args) {
@@ -128,7 +134,9 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  if (e == cudaSuccess) count_launches();
+  return e;
 }
 
 // Launch helpers (scan.cu).  All return cudaError_t of the launch.

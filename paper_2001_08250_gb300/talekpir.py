@@ -108,6 +108,7 @@ _SIGS = [
     ("tpir_graph_destroy", None, [_vp]),
     ("tpir_selftest_wait_timeout", ctypes.c_int, [_u32]),
     ("tpir_device_status", ctypes.c_int, []),
+    ("tpir_kernel_launches", ctypes.c_uint64, []),
     ("tpir_bloom_create", ctypes.c_int, [_vp, _u64, _u32, _u32, _u32]),
     ("tpir_bloom_insert", ctypes.c_int, [_vp, _vp]),
     ("tpir_bloom_insert_batch", ctypes.c_int, [_vp, _vp, _u32]),
@@ -184,6 +185,11 @@ def _stream(s) -> int:
 
 def device_status() -> int:
     return lib().tpir_device_status()
+
+
+def kernel_launches() -> int:
+    """Kernel launches the library has enqueued in this process so far."""
+    return int(lib().tpir_kernel_launches())
 
 
 class DB:

@@ -461,3 +461,27 @@ def test_pipelined_reads_of_several_tables_from_several_threads():
         for db in dbs:
             db.close()
     assert talekpir.device_status() == talekpir.OK
+
+
+def test_kernel_launch_counter_counts_the_reads_launches():
+    """tpir_kernel_launches counts every kernel the library enqueues: one
+    CTA-pair tensor-core launch for a 256-request read of a table that fits
+    one k-chunk, more when replies are initialised first, none for a call
+    that launches nothing (B = 0)."""
+    require_cuda()
+    n, d, z = 4096, 4, 1024
+    T = synth.table_bytes(n, d, z, seed=130)
+    R = synth.random_bits(256, n, seed=131)
+    with _db(n, d, z, T) as db:
+        dR, dO = to_dev(R), dev_out(256, d * z)
+        db.read_batch_async(dR, 256, dO)      # builds the transposed copy
+        db.sync()
+        k0 = talekpir.kernel_launches()
+        db.read_batch_async(dR, 256, dO)
+        db.sync()
+        assert talekpir.kernel_launches() - k0 == 1
+        k1 = talekpir.kernel_launches()
+        db.read_batch_async(dR, 0, dO)
+        assert talekpir.kernel_launches() == k1
+        assert np.array_equal(to_host(dO), oracle.read_batch(T, n, d, z, R))
+    assert talekpir.device_status() == talekpir.OK
