@@ -1,8 +1,8 @@
 /*
  * cpu_engine.c -- a multi-core CPU PIR read engine in the style of the
  * paper's CPU server (Section 9.2: the CPU engine streams the database once
- * per batch of reads and is bound by the memory bus).  It is a REPORTED
- * BASELINE ONLY, timed by the benchmark beside the oracle; it is not an
+ * per batch of reads and is bound by the memory bus).  It is a reported
+ * baseline only, timed by the benchmark beside the oracle; it is not an
  * oracle (the tests check it against oracle_read) and not part of the
  * library.  It shares no code with the oracle or the CUDA library.
  *
