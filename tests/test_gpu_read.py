@@ -485,3 +485,27 @@ def test_kernel_launch_counter_counts_the_reads_launches():
         assert talekpir.kernel_launches() == k1
         assert np.array_equal(to_host(dO), oracle.read_batch(T, n, d, z, R))
     assert talekpir.device_status() == talekpir.OK
+
+
+# CTA-pair tensor-core form: B just above one M-tile, blocks whose odd CTA has
+# no request, odd / even request-word counts (row pairs / rows staged by TMA),
+# n below one stage, an odd number of strips (the last pair half past the
+# row), tables longer than one 32 768-bucket k-chunk (partials XOR-combined)
+PAIR_SHAPES = [(63, 1, 256, 129), (300, 2, 512, 200), (513, 1, 4096, 384), (4096, 4, 256, 511),
+               (70001, 1, 448, 130)]
+
+
+@pytest.mark.parametrize("n,d,z,B", PAIR_SHAPES)
+def test_pair_tensor_form_bit_exact(n, d, z, B):
+    """Every reply of the tensor-core read on CTA pairs, plain and masked
+    (one k-chunk: keystream in the epilogue; several: masks written by the
+    reply initialisation), equals the oracle's."""
+    require_cuda()
+    T = synth.table_bytes(n, d, z, seed=140, table=n)
+    R = synth.random_bits(B, n, seed=141, table=n)
+    S = synth.mask_seeds(B, seed=142, table=n)
+    with _db(n, d, z, T) as db:
+        db.set_kernel(TENSOR)
+        assert np.array_equal(db.read_batch(R), oracle.read_batch(T, n, d, z, R))
+        assert np.array_equal(db.read_batch_masked(R, S), oracle.read_batch_masked(T, n, d, z, R, S))
+    assert talekpir.device_status() == talekpir.OK
