@@ -280,8 +280,8 @@ tpir_status tpir_tune_clear(void);
  * workload): job i reads B_i rows of d_req_bits_i against db_i into d_out_i.
  * Tables may differ in n, d and msg_bytes.  Jobs of >= 48 requests on rows of
  * >= 256 bytes go to the tensor-core kernel: those of more than 128 requests
- * on tables of >= 8192 buckets one CTA-pair launch each, the rest share one
- * launch (per request-staging mode), the others one
+ * on tables of >= 8192 buckets share one CTA-pair launch, the rest one
+ * single-CTA launch (each per request-staging mode), the others one
  * launch of the register-tiled kernel (a db forced to kernel 4 sends its jobs
  * to the Four-Russians kernel instead: one launch for jobs of up to 256
  * requests, one for larger ones; forced to 2, to the register-tiled one).  A

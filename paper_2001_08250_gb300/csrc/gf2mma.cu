@@ -943,20 +943,36 @@ __device__ __forceinline__ void p_commit_self(uint64_t* bar) {
                : "memory");
 }
 
-// Pair items: (pair strip, M-block, k-chunk), pair strip fastest; the pairs
-// take them round by round like the CTAs of the single-CTA kernel.
+// Pair items: (job, pair strip, M-block, k-chunk), pair strip fastest, the
+// jobs' items one after another; the pairs take them round by round like the
+// CTAs of the single-CTA kernel.
 struct PItem {
-  uint32_t pstrip, b0;
+  uint32_t job, pstrip, b0;
   uint64_t k0, k1;
 };
-__device__ __forceinline__ bool p_item(const GJob& J, uint32_t total, uint32_t pair, uint32_t npairs,
-                                       uint32_t r, PItem& it) {
+template <int NJ>
+__device__ __forceinline__ bool p_item(const GLaunch<NJ>& L, uint32_t pair, uint32_t npairs, uint32_t r,
+                                       PItem& it) {
   const uint32_t c = (r & 1u) ? npairs - 1u - pair : pair;
   const uint32_t item = c + r * npairs;
-  if (item >= total) return false;
+  if (item >= L.total_items) return false;
+  uint32_t lo = 0;
+  if constexpr (NJ > 1) {
+    uint32_t hi = L.njobs - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (L.jobs[mid].item_begin <= item)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+  }
+  const GJob& J = L.jobs[lo];
+  it.job = lo;
+  const uint32_t local = item - J.item_begin;
   const uint32_t nps = (J.n_strips + 1) / 2;
-  it.pstrip = item % nps;
-  const uint32_t rest = item / nps;
+  it.pstrip = local % nps;
+  const uint32_t rest = local / nps;
   it.b0 = (rest % J.n_mb) * 256u;
   it.k0 = static_cast<uint64_t>(rest / J.n_mb) * J.kc_rows;
   it.k1 = min(J.n, it.k0 + J.kc_rows);
@@ -968,20 +984,22 @@ struct PCursor {
   PItem it;
   bool valid;
 };
-__device__ __forceinline__ void p_cur_item(PCursor& c, const GJob& J, uint32_t total, uint32_t pair,
+template <int NJ>
+__device__ __forceinline__ void p_cur_item(PCursor& c, const GLaunch<NJ>& L, uint32_t pair,
                                            uint32_t npairs) {
-  c.valid = p_item(J, total, pair, npairs, c.r++, c.it);
+  c.valid = p_item(L, pair, npairs, c.r++, c.it);
   if (c.valid) c.ks = c.it.k0;
 }
-__device__ __forceinline__ void p_cur_next(PCursor& c, const GJob& J, uint32_t total, uint32_t pair,
+template <int NJ>
+__device__ __forceinline__ void p_cur_next(PCursor& c, const GLaunch<NJ>& L, uint32_t pair,
                                            uint32_t npairs) {
   c.ks += kGKStage;
-  if (c.ks >= c.it.k1) p_cur_item(c, J, total, pair, npairs);
+  if (c.ks >= c.it.k1) p_cur_item(c, L, pair, npairs);
 }
 
-template <int RM>
+template <int NJ, int RM>
 __global__ void __launch_bounds__(kPThreads, 1)
-    gf2_mma_pair_kernel(const __grid_constant__ GLaunch<1> L, int* status) {
+    gf2_mma_pair_kernel(const __grid_constant__ GLaunch<NJ> L, int* status) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[kPStages], pfull[kPStages], empty[kPStages], accf, acce, drain;
   __shared__ __align__(8) uint64_t raw_full[kPRaw], raw_empty[kPRaw];
@@ -993,10 +1011,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
   const uint32_t raw0 = stage0 + kPStages * kPStageBytes;
   volatile int* abort_flag = &s_abort;
   constexpr int kRawBytes = p_raw_bytes<RM>();
-  const GJob& J = L.jobs[0];
   const uint32_t rank = mb::cluster_rank();
   const uint32_t pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-  const uint32_t total = L.total_items;
 
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1050,8 +1066,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     if (lane == 0) {
       uint32_t p = 0;
       PCursor c{};
-      p_cur_item(c, J, total, pair, npairs);
-      for (; c.valid; p_cur_next(c, J, total, pair, npairs), ++p) {
+      p_cur_item(c, L, pair, npairs);
+      for (; c.valid; p_cur_next(c, L, pair, npairs), ++p) {
         const uint32_t rs = p % kPRaw, ph = (p / kPRaw) & 1u;
         if (!mb::wait_sleep(&raw_empty[rs], ph ^ 1u, abort_flag, status, kGWaitNs, 32)) break;
         const uint32_t dst = raw0 + rs * kRawBytes;
@@ -1059,17 +1075,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
                          mb::saddr(&raw_full[rs])),
                      "r"(kRawBytes)
                      : "memory");
+        const uint32_t jb = c.it.job;
         const int kb = static_cast<int>(c.ks >> 6);
         const int x0 = static_cast<int>(c.it.pstrip * 2u * kGCols + rank * kPCols);
-        g_tma_load(dst, &L.maps[0], x0, kb, &raw_full[rs]);
-        g_tma_load(dst + kPRawTile, &L.maps[0], x0 + kGCols, kb, &raw_full[rs]);
+        g_tma_load(dst, &L.maps[jb], x0, kb, &raw_full[rs]);
+        g_tma_load(dst + kPRawTile, &L.maps[jb], x0 + kGCols, kb, &raw_full[rs]);
         const int b = static_cast<int>(c.it.b0 + 128u * rank);
         if constexpr (RM == 1) {
-          g_tma_load(dst + kPRawTable, &L.rmaps[0], kb, b, &raw_full[rs]);
+          g_tma_load(dst + kPRawTable, &L.rmaps[jb], kb, b, &raw_full[rs]);
         } else {
-          g_tma_load(dst + kPRawTable, &L.rmaps[0], kb, b >> 1, &raw_full[rs]);
-          g_tma_load(dst + kPRawTable + 64 * 32, &L.rmaps_o[0], static_cast<int>(J.words64) + kb - 1,
-                     b >> 1, &raw_full[rs]);
+          g_tma_load(dst + kPRawTable, &L.rmaps[jb], kb, b >> 1, &raw_full[rs]);
+          g_tma_load(dst + kPRawTable + 64 * 32, &L.rmaps_o[jb],
+                     static_cast<int>(L.jobs[jb].words64) + kb - 1, b >> 1, &raw_full[rs]);
         }
       }
       for (uint32_t rs = 0; rs < static_cast<uint32_t>(kPRaw) && rs < p; ++rs) {
@@ -1091,8 +1108,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const uint32_t t = e >= static_cast<uint32_t>(kPCols) ? 1u : 0u, cc = e - t * kPCols;
     uint32_t iter = 0;
     PCursor c{};
-    p_cur_item(c, J, total, pair, npairs);
-    for (; c.valid; p_cur_next(c, J, total, pair, npairs), ++iter) {
+    p_cur_item(c, L, pair, npairs);
+    for (; c.valid; p_cur_next(c, L, pair, npairs), ++iter) {
       const uint32_t rs = iter % kPRaw, rph = (iter / kPRaw) & 1u;
       const uint32_t s = iter % kPStages, ph = (iter / kPStages) & 1u;
       if (!mb::wait(&raw_full[rs], rph, abort_flag, status, kGWaitNs)) break;
@@ -1127,7 +1144,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         if (lane == 0) mb::arrive(&raw_empty[rs]);
       }
       if (!mb::wait(&empty[s], ph ^ 1u, abort_flag, status, kGWaitNs)) break;
-      const bool store = table || c.it.b0 + 128u * rank + e < J.B;
+      const bool store = table || c.it.b0 + 128u * rank + e < L.jobs[c.it.job].B;
       if (store) {
         const uint32_t o = table ? stage0 + s * kPStageBytes + kPTileA + t * kPTileB + g_off(cc, 0)
                                  : stage0 + s * kPStageBytes + g_off(e, 0);
@@ -1147,8 +1164,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
       const uint32_t k = static_cast<uint32_t>(p_relay_index(warp));
       uint32_t iter = 0;
       PCursor c{};
-      p_cur_item(c, J, total, pair, npairs);
-      for (; c.valid; p_cur_next(c, J, total, pair, npairs), ++iter) {
+      p_cur_item(c, L, pair, npairs);
+      for (; c.valid; p_cur_next(c, L, pair, npairs), ++iter) {
         if (iter % kPStages != k) continue;
         const uint32_t ph = (iter / kPStages) & 1u;
         if (!mb::wait(&full[k], ph, abort_flag, status, kGWaitNs)) break;
@@ -1163,7 +1180,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       uint32_t is = 0, iph = 0;
       for (uint32_t r = 0;; ++r) {
         PItem it;
-        if (*abort_flag || !p_item(J, total, pair, npairs, r, it)) break;
+        if (*abort_flag || !p_item(L, pair, npairs, r, it)) break;
         bool ok = true;
         if (r >= 1) ok = mb::wait_cluster(&acce, (r - 1u) & 1u, abort_flag, status, kGWaitNs);
         bool have = ok && mb::wait(&full[is], iph, abort_flag, status, kGWaitNs) &&
@@ -1214,7 +1231,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     bool pdl_waited = false;
     for (uint32_t r = 0;; ++r) {
       PItem it;
-      if (*abort_flag || !p_item(J, total, pair, npairs, r, it)) break;
+      if (*abort_flag || !p_item(L, pair, npairs, r, it)) break;
       if (!mb::wait_sleep(&accf, r & 1u, abort_flag, status, kGWaitNs, 256)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!pdl_waited) {
@@ -1222,7 +1239,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
         pdl_waited = true;
       }
       const uint32_t lanes = (32u * quarter) << 16;
-      g_epilogue(J, tmem + lanes + kGCols * half, it.b0 + 128u * rank + 32u * quarter + lane,
+      g_epilogue(L.jobs[it.job], tmem + lanes + kGCols * half,
+                 it.b0 + 128u * rank + 32u * quarter + lane,
                  (2u * it.pstrip + half) * kGStripWords, kGStripWords);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -1408,12 +1426,12 @@ cudaError_t g_launch(GLaunch<NJ>& L, cudaStream_t st) {
 
 // Pairs a launch of the pair kernel can hold resident at once (clusters of
 // two CTAs of one SM each), once per request-staging mode.
-template <int RM>
+template <int NJ, int RM>
 int p_max_pairs() {
   static std::atomic<int> cached{0};
   int v = cached.load(std::memory_order_acquire);
   if (v) return v;
-  cudaError_t e = cudaFuncSetAttribute(gf2_mma_pair_kernel<RM>,
+  cudaError_t e = cudaFuncSetAttribute(gf2_mma_pair_kernel<NJ, RM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, p_smem<RM>());
   if (e != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
@@ -1428,7 +1446,7 @@ int p_max_pairs() {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&clusters, gf2_mma_pair_kernel<RM>, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&clusters, gf2_mma_pair_kernel<NJ, RM>, &cfg);
   if (e != cudaSuccess || clusters <= 0) return -1;
   cached.store(clusters, std::memory_order_release);
   return clusters;
@@ -1441,7 +1459,7 @@ template <int RM>
 cudaError_t g_launch_pair(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uint64_t* R,
                           uint32_t words64, uint32_t B, uint32_t* out, const uint8_t* seeds,
                           cudaStream_t st, const GSched* sched) {
-  const int pairs = p_max_pairs<RM>();
+  const int pairs = p_max_pairs<1, RM>();
   if (pairs <= 0) return cudaErrorNotSupported;
   int* status = device_status_word();
   if (!status) return cudaErrorInvalidSymbol;
@@ -1505,7 +1523,88 @@ cudaError_t g_launch_pair(const uint64_t* Tt, uint64_t n, uint32_t Wd, const uin
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  e = cudaLaunchKernelEx(&cfg, gf2_mma_pair_kernel<RM>, L, status);
+  e = cudaLaunchKernelEx(&cfg, gf2_mma_pair_kernel<1, RM>, L, status);
+  if (e == cudaSuccess) count_launches();
+  return e;
+}
+
+// Up to kGMultiJobs jobs of one request-staging mode on CTA pairs in one
+// persistent launch: every job's items hold whole k-chunks of up to 32 768
+// buckets (or the tuned size), the jobs in descending item cost, dealt round
+// by round over the pairs.
+template <int RM>
+cudaError_t g_launch_pair_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
+  const int pairs = p_max_pairs<kGMultiJobs, RM>();
+  if (pairs <= 0) return cudaErrorNotSupported;
+  int* status = device_status_word();
+  if (!status) return cudaErrorInvalidSymbol;
+  std::vector<GJob> js;
+  std::vector<const M4Request*> src;
+  std::vector<uint64_t> cost;
+  for (uint32_t i = 0; i < count; ++i) {
+    const M4Request& q = reqs[i];
+    if (q.B == 0) continue;
+    if (!q.Tt) return cudaErrorInvalidValue;
+    GJob j = g_job(q.R, q.words64, q.B, q.out, q.seeds, q.n, q.Wd);
+    j.kc_rows = g_clamp_rows(q.kc_rows ? q.kc_rows : kGMaxCount, q.n);
+    const uint64_t kcs = (q.n + j.kc_rows - 1) / j.kc_rows;
+    j.split = kcs > 1 ? 1u : q.seeds ? 2u : 0u;
+    j.req_tma = RM;
+    js.push_back(j);
+    src.push_back(&q);
+    cost.push_back(std::min<uint64_t>(j.kc_rows, q.n));
+  }
+  if (js.empty()) return cudaSuccess;
+  std::vector<size_t> order(js.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+  GLaunch<kGMultiJobs> L{};
+  L.njobs = 0;
+  L.nbuf = 1;
+  uint64_t items = 0;
+  bool any_split = false;
+  for (size_t oi : order) {
+    GJob j = js[oi];
+    const M4Request& q = *src[oi];
+    const uint64_t kcs = (j.n + j.kc_rows - 1) / j.kc_rows;
+    j.item_begin = static_cast<uint32_t>(items);
+    items += static_cast<uint64_t>((j.n_strips + 1) / 2) * j.n_mb * kcs;
+    if (items > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+    const uint64_t nw = (j.n + 63) / 64;
+    cudaError_t e = g_table_map(q.Tt, j.n, j.Wd, &L.maps[L.njobs], kPCols);
+    if (e != cudaSuccess) return e;
+    if (RM == 1) {
+      if (g_req_map(q.R, nw, q.B, q.words64, kGStageWords, 128, &L.rmaps[L.njobs]) != cudaSuccess)
+        return cudaErrorInvalidValue;
+    } else {
+      if (g_req_map(q.R, nw, (q.B + 1) / 2, 2ull * q.words64, kGStageWords, 64, &L.rmaps[L.njobs]) !=
+              cudaSuccess ||
+          g_req_map(q.R, q.words64 + nw, q.B / 2, 2ull * q.words64, kGStageWords + 2, 64,
+                    &L.rmaps_o[L.njobs]) != cudaSuccess)
+        return cudaErrorInvalidValue;
+    }
+    any_split |= j.split == 1;
+    L.jobs[L.njobs++] = j;
+  }
+  L.total_items = static_cast<uint32_t>(items);
+  cudaError_t e = cudaSuccess;
+  if (any_split) e = launch_pdl(gf2_init_kernel<kGMultiJobs>, dim3(64, L.njobs), dim3(256), 0, st, L);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * std::min<uint64_t>(items, pairs)));
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = p_smem<RM>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  e = cudaLaunchKernelEx(&cfg, gf2_mma_pair_kernel<kGMultiJobs, RM>, L, status);
   if (e == cudaSuccess) count_launches();
   return e;
 }
@@ -1671,25 +1770,35 @@ cudaError_t g_launch_multi(const M4Request* reqs, uint32_t count, uint32_t mode,
 cudaError_t launch_gf2_mma_multi(const M4Request* reqs, uint32_t count, cudaStream_t st) {
   if (count > TPIR_MAX_JOBS) return cudaErrorInvalidValue;
   // Jobs of more than 128 requests whose rows TMA can stage, on tables of at
-  // least kPairMinN buckets, run on CTA pairs, one launch each (a pair launch
-  // holds one job; on smaller tables its fixed cost outweighs the gain: the
-  // 64-table benchmark took 16.4 ms with this bound, 16.6 ms pairing every
-  // such job, 17.7 ms pairing none); the others are grouped by how TMA stages
-  // their request words (rows, row pairs, per-thread loads), in launches of
-  // at most kGMultiJobs jobs (the kernel parameters hold three tensor maps
-  // per job), in stream order.
+  // least kPairMinN buckets, run on CTA pairs (one persistent launch per
+  // staging mode; on smaller tables the pair form's fixed cost outweighed its
+  // gain); the others are grouped by how TMA stages their request words
+  // (rows, row pairs, per-thread loads); launches of at most kGMultiJobs jobs
+  // (the kernel parameters hold three tensor maps per job), in stream order.
   constexpr uint64_t kPairMinN = 8192;
   auto paired = [](const M4Request& q) {
     return q.B > 128 && !q.loads && g_req_mode(q.R, q.words64) != 0 && q.n >= kPairMinN;
   };
-  for (uint32_t i = 0; i < count; ++i) {
-    const M4Request& q = reqs[i];
-    if (!q.B || !paired(q)) continue;
-    if (!q.Tt) return cudaErrorInvalidValue;
-    const GSched sched{2u, q.kc_rows, 0u};
-    const cudaError_t e = launch_gf2_mma(q.Tt, q.n, q.Wd, q.R, q.words64, q.B, q.out, q.seeds, st,
-                                         q.kc_rows ? &sched : nullptr);
-    if (e != cudaSuccess) return e;
+  for (uint32_t rm : {1u, 2u}) {
+    std::vector<M4Request> part;
+    for (uint32_t i = 0; i < count; ++i)
+      if (reqs[i].B && paired(reqs[i]) && g_req_mode(reqs[i].R, reqs[i].words64) == rm)
+        part.push_back(reqs[i]);
+    for (size_t i = 0; i < part.size(); i += kGMultiJobs) {
+      const uint32_t c = static_cast<uint32_t>(std::min<size_t>(kGMultiJobs, part.size() - i));
+      cudaError_t e = rm == 1 ? g_launch_pair_multi<1>(part.data() + i, c, st)
+                              : g_launch_pair_multi<2>(part.data() + i, c, st);
+      if (e == cudaErrorNotSupported) {  // no room for the pairs' clusters: one read each
+        e = cudaSuccess;
+        for (uint32_t k = 0; k < c && e == cudaSuccess; ++k) {
+          const M4Request& q = part[i + k];
+          const GSched sched{2u, q.kc_rows, 0u};
+          e = launch_gf2_mma(q.Tt, q.n, q.Wd, q.R, q.words64, q.B, q.out, q.seeds, st,
+                             q.kc_rows ? &sched : nullptr);
+        }
+      }
+      if (e != cudaSuccess) return e;
+    }
   }
   for (uint32_t mode : {1u, 2u, 0u}) {
     std::vector<M4Request> part;
