@@ -375,6 +375,34 @@ def main() -> None:
     tc_tflops = gf2_mma_flops(n, row, B_HEAD) / (launch_ms * 1e-3) / 1e12
     smem_peak = smem_peak_tbs(sm_mhz)
 
+    # ---- the same step through many-table calls (64 batches per persistent
+    # launch): reported beside the headline, which reads batch by batch
+    multi_call = None
+    if "head" in args.legs:
+        mjobs = [(dbs[i % COPIES], min(B_HEAD, USERS - b0), dR[b0:b0 + B_HEAD], dO[b0:b0 + B_HEAD])
+                 for i, b0 in enumerate(range(0, USERS, B_HEAD))]
+
+        def multi_step():
+            for j0 in range(0, len(mjobs), 64):
+                talekpir.read_multi_async(mjobs[j0:j0 + 64], stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                multi_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0 = talekpir.kernel_launches()
+        e0.record(stream)
+        for _ in range(args.steps):
+            multi_step()
+        e1.record(stream)
+        mk = talekpir.kernel_launches() - k0
+        torch.cuda.synchronize()
+        mms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        multi_call = {"reads_per_s": USERS * world / (mms * 1e-3), "ms_per_step": mms,
+                      "launches_per_step": mk / args.steps,
+                      "call": "tpir_read_multi_async, 64 batches per call"}
+
     # ---- the same batches on the Four-Russians kernel (shared-memory-bound)
     m4 = None
     if "head_m4rm" in args.legs:
@@ -536,6 +564,7 @@ def main() -> None:
                                "traffic": TRAFFIC_PLAIN_B1,
                                "kernel": "plain_tma_kernel", "peak_basis": "of measured" if peaks else "of fallback"},
             "legs": legs,
+            "head_many_table_calls": multi_call,
             "masked": masked,
             "sharded": sharded,
             "autotune": tune,
