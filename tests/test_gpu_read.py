@@ -509,3 +509,45 @@ def test_pair_tensor_form_bit_exact(n, d, z, B):
         assert np.array_equal(db.read_batch(R), oracle.read_batch(T, n, d, z, R))
         assert np.array_equal(db.read_batch_masked(R, S), oracle.read_batch_masked(T, n, d, z, R, S))
     assert talekpir.device_status() == talekpir.OK
+
+
+def test_multi_table_pair_launch_bit_exact():
+    """Large batches on tables of >= 8192 buckets share one persistent
+    CTA-pair launch per request-staging mode in a many-table call: rows of
+    an even word count (TMA rows) and of an odd one (row pairs), a masked job
+    (keystream in the epilogue), a table of two k-chunks (partials
+    XOR-combined into initialised replies), next to a job of <= 128 requests
+    in the single-CTA launch; every reply equals the oracle's, directly and
+    replayed from a captured graph."""
+    torch = require_cuda()
+    shapes = [(8192, 1, 256, 129, False), (9000, 2, 256, 256, False), (16385, 1, 512, 300, False),
+              (40000, 1, 256, 200, False), (12288, 1, 256, 140, True), (8192, 1, 256, 100, False)]
+    dbs, jobs, exp = [], [], []
+    for i, (n, d, z, B, masked) in enumerate(shapes):
+        T = synth.table_bytes(n, d, z, seed=150, table=i)
+        R = synth.random_bits(B, n, seed=151, table=i)
+        db = _db(n, d, z, T)
+        dbs.append(db)
+        if masked:
+            S = synth.mask_seeds(B, seed=152, table=i)
+            dS = torch.from_numpy(np.ascontiguousarray(S)).cuda()
+            jobs.append((db, B, to_dev(R), dev_out(B, d * z), dS))
+            exp.append(oracle.read_batch_masked(T, n, d, z, R, S))
+        else:
+            jobs.append((db, B, to_dev(R), dev_out(B, d * z)))
+            exp.append(oracle.read_batch(T, n, d, z, R))
+    try:
+        talekpir.read_multi_async(jobs)
+        for job, e in zip(jobs, exp):
+            assert np.array_equal(to_host(job[3]), e), job[0].n
+        for job in jobs:
+            job[3].zero_()
+        g = talekpir.MultiGraph(jobs)
+        g.launch()
+        for job, e in zip(jobs, exp):
+            assert np.array_equal(to_host(job[3]), e), job[0].n
+        g.close()
+    finally:
+        for db in dbs:
+            db.close()
+    assert talekpir.device_status() == talekpir.OK
